@@ -1,0 +1,83 @@
+"""Seeded synthetic inputs shared by the tests, the smoke check and the bench.
+
+This module holds no arithmetic of the hashing method: it only draws
+64-bit words.  Element k of stream ``seed`` is the SplitMix64 finaliser
+(Steele, Lea and Flood, "Fast splittable pseudorandom number generators",
+OOPSLA 2014) applied to ``key(seed) + (k + 1) * 0x9E3779B97F4A7C15``; a word
+that is not below ``bound`` is re-mixed until it is (an ``O(2^-32)`` event for
+the Goldilocks bound), so every element depends only on (seed, k) and any
+slice can be generated independently.
+
+Seeds: workload ``cfg`` uses ``0x5EED0000 + cfg``; tree ``i`` of a batch uses
+``tree_seed(seed, i)``.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+M1 = np.uint64(0xBF58476D1CE4E5B9)
+M2 = np.uint64(0x94D049BB133111EB)
+FIELD_BOUND = 0xFFFFFFFF00000001  # inputs are drawn uniform in [0, bound)
+
+
+def _mix(z: np.ndarray) -> np.ndarray:
+    z = z.copy()
+    z ^= z >> np.uint64(30)
+    z *= M1
+    z ^= z >> np.uint64(27)
+    z *= M2
+    z ^= z >> np.uint64(31)
+    return z
+
+
+def _key(seed: int) -> np.uint64:
+    return _mix(np.array([seed & 0xFFFFFFFFFFFFFFFF], dtype=np.uint64))[0]
+
+
+def words(seed: int, count: int, start: int = 0, bound: int | None = FIELD_BOUND,
+          chunk: int = 1 << 22) -> np.ndarray:
+    """``count`` words of stream ``seed`` starting at element ``start``."""
+    out = np.empty(count, dtype=np.uint64)
+    key = _key(seed)
+    with np.errstate(over="ignore"):
+        for lo in range(0, count, chunk):
+            hi = min(count, lo + chunk)
+            idx = np.arange(start + lo + 1, start + hi + 1, dtype=np.uint64)
+            z = _mix(key + idx * GOLDEN)
+            if bound is not None:
+                b = np.uint64(bound)
+                bad = z >= b
+                while bad.any():
+                    z[bad] = _mix(z[bad])
+                    bad = z >= b
+            out[lo:hi] = z
+    return out
+
+
+def matrix(seed: int, rows: int, cols: int, bound: int | None = FIELD_BOUND) -> np.ndarray:
+    """A (rows, cols) uint64 matrix, row-major, element (r, c) = word r*cols+c."""
+    return words(seed, rows * cols, bound=bound).reshape(rows, cols)
+
+
+def tree_seed(seed: int, tree: int) -> int:
+    """Per-tree sub-seed of a batch."""
+    return int(_mix(np.array([(seed * 0x100000001B3 + tree + 1) & 0xFFFFFFFFFFFFFFFF],
+                             dtype=np.uint64))[0])
+
+
+def config_seed(cfg: int) -> int:
+    return 0x5EED0000 + cfg
+
+
+def integers(seed: int, count: int, lo: int, hi: int) -> np.ndarray:
+    """``count`` integers uniform in [lo, hi] (inclusive), from stream ``seed``."""
+    span = hi - lo + 1
+    w = words(seed, count, bound=None)
+    return (lo + (w % np.uint64(span)).astype(np.int64)).astype(np.int64)
+
+
+def uniform01(seed: int, count: int) -> np.ndarray:
+    """``count`` doubles uniform in [0, 1) from the top 53 bits of the words."""
+    w = words(seed, count, bound=None)
+    return (w >> np.uint64(11)).astype(np.float64) * (1.0 / (1 << 53))
