@@ -1,0 +1,318 @@
+#!/usr/bin/env python
+"""Benchmark of the Poseidon-12 / Goldilocks Merkle build on GB300.
+
+One step = one whole Merkle tree (Sec. 4.2) over 2^22 synthetic leaf rows of
+8 Goldilocks words: leaf sponge hashing, then every level up to the root --
+8,388,607 permutations, all in one persistent kernel launch.  The rows
+(256 MiB) stay resident in HBM; they are larger than the 129 MB L2, so no
+flush is needed between steps.
+
+Printed (rank 0, one JSON line): throughput in permutations/s over the
+whole job, the build time in ms, the roofline of the kernel against the
+integer-multiply pipe, an end-to-end figure through the C ABI with the rows
+copied from pinned host memory every step, GPU clocks sampled during the
+timed region, and the CPU oracle timed on a bounded sample.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Poseidon-12 perms/s and 2^22-leaf Merkle build ms; % of IMAD roofline"
+# 32-bit multiply results of one permutation in the optimised form with the
+# dense 12x12 MDS: S-boxes 118*(2*6+2*8) + full-round MDS 8*144*8 +
+# partial-round sparse layers 22*23*8.
+MUL_RESULTS_PER_PERM = 118 * (2 * 6 + 2 * 8) + 8 * 144 * 8 + 22 * 23 * 8
+IMAD_RESULTS_PER_CLK_SM = 64  # 32-bit multiply results per clock per SM
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--log-n", type=int, default=22)
+    ap.add_argument("--width", type=int, default=8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def workload(log_n, width):
+    n = 1 << log_n
+    chunks = max(1, (width + 7) // 8)
+    perms = n * chunks + (n - 1)
+    name = f"merkle 2^{log_n} leaves x width {width}: leaf sponge + all levels to the root"
+    return n, perms, name
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+# ------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.lines = []
+        self.proc = None
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if gpu_id:
+            cmd += ["-i", gpu_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if parts[5 + k].lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------ oracle timing
+def oracle_rate(width, seconds, seed=0x5EED0003):
+    """Permutations/s of the CPU oracle (all host cores) on a bounded tree."""
+    import numpy as np  # noqa: F401
+    import oracle
+    import pg_synth
+    cores = os.cpu_count() or 1
+    log_n = 8
+    while True:
+        n = 1 << log_n
+        rows = pg_synth.matrix(seed, n, width)
+        t0 = time.perf_counter()
+        oracle.merkle_build(rows, nthreads=cores)
+        dt = time.perf_counter() - t0
+        perms = workload(log_n, width)[1]
+        if dt >= seconds / 4 or log_n >= 22:
+            return perms / dt, cores, log_n, dt, perms
+        grow = max(1, min(4, int((seconds / max(dt, 1e-3)) ** 0.5).bit_length() - 1))
+        log_n = min(22, log_n + grow)
+
+
+def oracle_step_size(width, target_s):
+    """Largest 2^k-leaf tree the oracle builds in about target_s seconds."""
+    rate, cores, log_n, dt, perms = oracle_rate(width, min(target_s, 4.0))
+    while log_n < 22 and workload(log_n + 1, width)[1] / rate <= target_s:
+        log_n += 1
+    while log_n > 4 and workload(log_n, width)[1] / rate > 1.5 * target_s:
+        log_n -= 1
+    return log_n, cores
+
+
+# ------------------------------------------------------------ reference arm
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    import pg_synth
+    n, perms_full, name = workload(args.log_n, args.width)
+    log_s, cores = oracle_step_size(args.width, target_s=4.0)
+    ns, perms, _ = workload(log_s, args.width)
+    rows = pg_synth.matrix(0x5EED0003, ns, args.width)
+    for _ in range(args.warmup):
+        oracle.merkle_build(rows, nthreads=cores)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.merkle_build(rows, nthreads=cores)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = perms * args.steps / tot
+    sample = f"2^{log_s}-leaf subtree of the same workload (width {args.width}), {perms} permutations per step"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "perms/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": name, "leaves": n, "width": args.width,
+                   "parallelism": "cpu oracle, level-parallel threads"},
+        "cpu_baseline": {"value": value, "unit": "perms/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "perms/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------ our arm
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_2506_09505_gb300 as pg
+    import pg_synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    pg.load(build_if_missing=True)
+    pg.init(local)
+
+    n, perms, name = workload(args.log_n, args.width)
+    rows_np = pg_synth.matrix(pg_synth.config_seed(3) + rank, n, args.width)
+    rows = torch.from_numpy(rows_np.view(np.int64)).cuda()
+    nodes = torch.empty((2 * n - 1, 4), dtype=torch.int64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(max(args.warmup, 0)):
+        pg.merkle_build(rows, nodes)
+    props = torch.cuda.get_device_properties(local)
+    gpu_id = None
+    try:
+        gpu_id = "GPU-" + str(props.uuid) if not str(props.uuid).startswith("GPU-") else str(props.uuid)
+    except Exception:
+        gpu_id = None
+    barrier()
+    sampler = ClockSampler(gpu_id)
+    time.sleep(0.4)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    ev[0].record(stream)
+    for k in range(args.steps):
+        pg.merkle_build(rows, nodes)
+        ev[k + 1].record(stream)
+    barrier()
+    clocks = sampler.stop()
+    step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+    total_ms = ev[0].elapsed_time(ev[-1])
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms = total_ms / args.steps
+    value = perms * world * args.steps / (total_ms / 1e3)
+
+    # end to end through the public call: pinned host rows -> device, build,
+    # root back to the host, every step
+    host_rows = torch.from_numpy(rows_np.view(np.int64)).pin_memory()
+    dev_rows = torch.empty_like(rows)
+    for _ in range(2):
+        dev_rows.copy_(host_rows, non_blocking=True)
+        pg.merkle_build(dev_rows, nodes, want_root=True)
+    barrier()
+    e_steps = max(3, min(args.steps, 10))
+    t0 = time.perf_counter()
+    for _ in range(e_steps):
+        dev_rows.copy_(host_rows, non_blocking=True)
+        pg.merkle_build(dev_rows, nodes, want_root=True)
+    e_s = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e_s = float(t.item())
+    e2e = {"value": perms * world * e_steps / e_s, "unit": "perms/s",
+           "h2d_bytes_per_step": int(rows_np.nbytes), "d2h_bytes_per_step": 32,
+           "ms_per_step": 1e3 * e_s / e_steps}
+
+    peaks = measured_peaks()
+    sms = props.multi_processor_count
+    max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = IMAD_RESULTS_PER_CLK_SM * sms * max_mhz * 1e6 / 1e12  # T results/s
+    achieved = perms * MUL_RESULTS_PER_PERM / (ms / 1e3) / 1e12
+    roofline = {
+        "bound": "alu", "kernel": "k_merkle",
+        "achieved": achieved, "peak": peak, "unit": "T mul32-results/s",
+        "frac": achieved / peak,
+        "peak_basis": f"{IMAD_RESULTS_PER_CLK_SM} x {sms} SMs x {max_mhz:.0f} MHz (sm_max_mhz)",
+        "traffic": None,
+        "algorithmic_bytes_per_launch": int(rows_np.nbytes + 32 * (2 * n - 1)),
+    }
+    if clocks and clocks.get("sm_mhz"):
+        roofline["frac_at_sampled_clock"] = achieved / (IMAD_RESULTS_PER_CLK_SM * sms * clocks["sm_mhz"] * 1e6 / 1e12)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "perms/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u64", "data": "synthetic",
+        "config": {"workload": name, "leaves": n, "width": args.width, "perms_per_tree": perms,
+                   "trees_per_gpu": 1, "parallelism": f"replicas x{world} (independent trees)",
+                   "l2": "inputs larger than L2 (rows 256 MiB/step at width 8), no flush"},
+        "build_ms": ms, "build_ms_min": min(step_ms),
+        "roofline": roofline, "e2e": e2e, "gpu_launches": args.steps, "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, cores, log_s, dt, sp = oracle_rate(args.width, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": rate, "unit": "perms/s", "cores": cores, "kind": "oracle",
+                                "sample": f"2^{log_s}-leaf tree of width {args.width} "
+                                          f"({sp} permutations, {dt:.1f} s), level-parallel threads"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

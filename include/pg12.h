@@ -1,0 +1,140 @@
+/*
+ * pg12.h -- C ABI of the GB300 Poseidon-12 / Goldilocks Merkle library.
+ *
+ * Everything here follows arXiv 2506.09505:
+ *   field        Eq. 1: p = 2^64 - 2^32 + 1; an element is canonical when
+ *                0 <= e < p (Sec. 2.4).
+ *   permutation  Alg. 1 and Sec. 2.4: width 12, S-box x^7, 4 + 22 + 4 rounds
+ *                (HALF_FULL_ROUNDS = 4, PARTIAL_ROUNDS = 22), 12x12 MDS layer.
+ *   sponge       Sec. 2.4: rate 8 (chunks of eight elements), capacity 4,
+ *                4-element digest; overwrite mode, short last chunk
+ *                zero-filled.
+ *   Merkle tree  Sec. 2.4 and Sec. 4.2: leaves are hashes of the data rows,
+ *                each parent hashes the concatenation of its two children,
+ *                level by level up to the root.
+ *
+ * Conventions shared by every call
+ *   - Elements are uint64_t, little-endian words.  Any 64-bit input word is
+ *     accepted and taken mod p; every output word is canonical (< p).
+ *   - "dev" pointers are CUDA device pointers on the device given to
+ *     pg_init(); the caller allocates and owns every buffer.  The library
+ *     owns only its constant tables and a small workspace it allocates in
+ *     pg_init() (released by pg_shutdown()).
+ *   - Calls are asynchronous on `stream` (a cudaStream_t passed as void*;
+ *     NULL = the legacy default stream) unless stated otherwise.  Argument
+ *     errors are detected on the host and returned before anything is
+ *     launched.  CUDA errors map to PG_ERR_CUDA; pg_last_error() gives the
+ *     text.  Nothing in the library spins on the device.
+ *   - Not thread-safe: calls that share one pg_init() context must be
+ *     serialised by the caller.
+ */
+#ifndef PG12_H
+#define PG12_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PG_OK = 0,
+    PG_ERR_INVALID_ARG = 1, /* null pointer, zero width, bad sizes            */
+    PG_ERR_NOT_POW2 = 2,    /* leaf count is not a power of two               */
+    PG_ERR_OOM = 3,         /* workspace or host allocation failed            */
+    PG_ERR_CUDA = 4,        /* a CUDA runtime call failed                     */
+    PG_ERR_TIMEOUT = 5,     /* a bounded host wait expired                    */
+    PG_ERR_PARAMS = 6,      /* parameter set missing, malformed or inconsistent */
+    PG_ERR_NOT_INIT = 7     /* pg_init() has not succeeded on this process    */
+} pg_status;
+
+/* Library version, e.g. "pg12 1.0 sm_103a". */
+const char *pg_version(void);
+
+/* Text of the most recent error of this process ("" if none). */
+const char *pg_last_error(void);
+
+/*
+ * pg_init -- select `device`, build parameter set pg12_v1 on the host and
+ * upload the optimised-form constants (Alg. 1) to the device.
+ *   device       CUDA ordinal.
+ *   params_path  must be NULL (built-in pg12_v1); any other value returns
+ *                PG_ERR_PARAMS.
+ * Idempotent for the same device.  Synchronous.  Allocates the workspace
+ * used by pg_merkle_build / pg_merkle_build_batch.
+ */
+pg_status pg_init(int device, const char *params_path);
+
+/* Release the workspace.  Safe to call when not initialised. */
+pg_status pg_shutdown(void);
+
+/*
+ * pg_params_export -- host copy of the plain parameter set this library
+ * generated (Sec. 2.4: round constants C and MDS matrix M of Alg. 1, before
+ * the optimised rewrite):
+ *   rc   host, 30*12 words, rc[r*12 + i] = constant of round r, cell i;
+ *   mds  host, 12*12 words, row-major, new_i = sum_j mds[i*12+j] * x_j.
+ * Either pointer may be NULL.  Host-only; works without a GPU.
+ */
+pg_status pg_params_export(uint64_t *rc, uint64_t *mds);
+
+/*
+ * pg_params_export_optimized -- host copy of the optimised-form constants
+ * that the kernels use (Alg. 1's C, M, S after the sparse rewrite):
+ *   full_rc   8*12 words: constants added before the S-box of full rounds
+ *             0..3 and 26..29 (in that order);
+ *   mds       12*12 words: dense matrix of full rounds 0,1,2,26..29;
+ *   pre       12*12 words: dense matrix of full round 3 (transition matrix);
+ *   part_rc   22 words: scalar added to cell 0 before the S-box of partial
+ *             round r (r = 0..21);
+ *   part_v    22*12 words: first row of the sparse matrix of partial round r
+ *             (new_0 = sum_j v[j] x_j);
+ *   part_w    22*11 words: first column below the diagonal
+ *             (new_i = x_i + w[i-1] x_0 for i >= 1).
+ * Any pointer may be NULL.  Host-only; works without a GPU.
+ */
+pg_status pg_params_export_optimized(uint64_t *full_rc, uint64_t *mds, uint64_t *pre,
+                                     uint64_t *part_rc, uint64_t *part_v, uint64_t *part_w);
+
+/*
+ * pg_permute_batch -- Alg. 1: one Poseidon-12 permutation of each of `n`
+ * independent states, in place.
+ *   states  dev, n*12 words, state k at states[12k .. 12k+11]; 8-byte aligned.
+ *   n       number of states; 0 is a no-op.
+ */
+pg_status pg_permute_batch(uint64_t *states, size_t n, void *stream);
+
+/*
+ * pg_hash_rows -- Sec. 2.4 sponge over every row of a row-major matrix.
+ *   rows     dev, n_rows*width words, row r at rows[r*width ..]; 8-byte aligned.
+ *   n_rows   number of rows (0 = no-op).
+ *   width    elements per row, >= 1 (0 -> PG_ERR_INVALID_ARG).  Rows use
+ *            ceil(width/8) permutations; a short last chunk is zero-filled.
+ *   digests  dev, n_rows*4 words, digest r at digests[4r ..].
+ */
+pg_status pg_hash_rows(const uint64_t *rows, size_t n_rows, size_t width, uint64_t *digests,
+                       void *stream);
+
+/*
+ * pg_merkle_build -- Sec. 4.2: whole Merkle tree over n_leaves rows.
+ *   rows      dev, n_leaves*width words, row-major.
+ *   n_leaves  power of two >= 1 (otherwise PG_ERR_NOT_POW2).
+ *   width     elements per row, >= 1.
+ *   nodes     dev, (2*n_leaves-1)*4 words, level-major: level 0 (the
+ *             n_leaves leaf digests), then level 1 (n_leaves/2 nodes), ...,
+ *             the root in the last 4 words.  Node k of level l is the hash
+ *             of nodes 2k and 2k+1 of level l-1.
+ *   root_out  host, 4 words, or NULL.  When non-NULL the call synchronises
+ *             `stream` and copies the root there.
+ * Uses the library workspace (allocated in pg_init) for its tile counters;
+ * concurrent builds on different streams are not supported.
+ */
+pg_status pg_merkle_build(const uint64_t *rows, size_t n_leaves, size_t width, uint64_t *nodes,
+                          uint64_t *root_out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PG12_H */

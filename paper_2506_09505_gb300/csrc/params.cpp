@@ -1,0 +1,213 @@
+// Host-side parameter construction for the device permutation.
+//
+// 1. Parameter set pg12_v1 (the paper prints none of the constants C, M, S
+//    that Alg. 1 names): the Poseidon paper's Grain-LFSR procedure seeded
+//    with (prime field, x^alpha S-box, n = 64, t = 12, R_F = 8, R_P = 22) --
+//    80-bit register, 160 discarded clocks, self-shrinking output (a bit is
+//    emitted only when the clock before it produced a 1), 64-bit big-endian
+//    words rejected when >= p.  360 round constants come first, then 24
+//    points x_0..x_11, y_0..y_11 for the Cauchy matrix M[i][j] = 1/(x_i+y_j);
+//    the 24 are drawn again if any two coincide or some x_i + y_j = 0.
+// 2. The sparse rewrite of the 22 partial rounds that Alg. 1 uses
+//    (MDSPartial with its vec[2][12] per round), derived here from (C, M):
+//    - constants: a partial round's S-box touches cell 0 only, so cells
+//      1..11 of its constant are carried through the S-box and the matrix
+//      into the next round's constant; each partial round keeps one scalar
+//      and the remainder lands in the constant of the first full round of
+//      the second half;
+//    - matrices: going backwards from the last partial round, the round's
+//      matrix N is factored as N = A * B with B = diag(1, N_hat) (which
+//      commutes with a cell-0 S-box and with cell-0 constants) and A sparse,
+//      A = [[n00, v^T], [n_col, I]] with v = N_hat^-T n_row; B is pushed
+//      into the previous round, so full round 3 ends with the dense
+//      "transition" matrix B_first * M.
+#include "pg12_internal.h"
+
+#include <cstring>
+#include <vector>
+
+namespace pg12 {
+namespace host {
+
+static inline uint64_t fp_reduce(unsigned __int128 v) { return (uint64_t)(v % kP); }
+uint64_t fp_add(uint64_t a, uint64_t b) { return fp_reduce((unsigned __int128)a + b); }
+uint64_t fp_sub(uint64_t a, uint64_t b) { return fp_add(a, b == 0 ? 0 : kP - (b % kP)); }
+uint64_t fp_mul(uint64_t a, uint64_t b) { return fp_reduce((unsigned __int128)a * b); }
+uint64_t fp_pow(uint64_t a, uint64_t e) {
+    uint64_t acc = 1, base = a % kP;
+    for (; e; e >>= 1, base = fp_mul(base, base))
+        if (e & 1) acc = fp_mul(acc, base);
+    return acc;
+}
+uint64_t fp_inv(uint64_t a) { return fp_pow(a, kP - 2); }
+
+// ---------------------------------------------------------------- Grain LFSR
+namespace {
+class Grain {
+  public:
+    Grain(unsigned field, unsigned sbox, unsigned n, unsigned t, unsigned rf, unsigned rp) {
+        // register bits s[0] (oldest) .. s[79]; packed as a bit queue
+        int k = 0;
+        auto push = [&](uint64_t v, int bits) {
+            for (int b = bits - 1; b >= 0; --b) s_[k++] = (uint8_t)((v >> b) & 1u);
+        };
+        push(field, 2);
+        push(sbox, 4);
+        push(n, 12);
+        push(t, 12);
+        push(rf, 10);
+        push(rp, 10);
+        push(0x3FFFFFFFull, 30);
+        head_ = 0;
+        for (int i = 0; i < 160; ++i) step();
+    }
+    // One register clock; the taps are s[0], s[13], s[23], s[38], s[51], s[62].
+    int step() {
+        auto at = [&](int i) { return (int)s_[(head_ + i) % 80]; };
+        int nb = at(0) ^ at(13) ^ at(23) ^ at(38) ^ at(51) ^ at(62);
+        s_[head_] = (uint8_t)nb;  // the oldest slot becomes the newest bit
+        head_ = (head_ + 1) % 80;
+        return nb;
+    }
+    int bit() {
+        for (;;) {
+            int gate = step();
+            int out = step();
+            if (gate) return out;
+        }
+    }
+    uint64_t word64() {
+        uint64_t w = 0;
+        for (int i = 0; i < 64; ++i) w = (w << 1) | (uint64_t)bit();
+        return w;
+    }
+    uint64_t element() {
+        uint64_t w;
+        do { w = word64(); } while (w >= kP);
+        return w;
+    }
+
+  private:
+    uint8_t s_[80];
+    int head_;
+};
+}  // namespace
+
+void generate_plain(PlainParams &pp) {
+    Grain g(1, 0, 64, kT, kRF, kRP);
+    for (int r = 0; r < kRounds; ++r)
+        for (int i = 0; i < kT; ++i) pp.rc[r][i] = g.element();
+    for (;;) {
+        uint64_t pts[2 * kT];
+        for (auto &p : pts) p = g.element();
+        bool good = true;
+        for (int a = 0; a < 2 * kT && good; ++a)
+            for (int b = 0; b < a; ++b)
+                if (pts[a] == pts[b]) { good = false; break; }
+        for (int i = 0; i < kT && good; ++i)
+            for (int j = 0; j < kT; ++j)
+                if (fp_add(pts[i], pts[kT + j]) == 0) { good = false; break; }
+        if (!good) continue;
+        for (int i = 0; i < kT; ++i)
+            for (int j = 0; j < kT; ++j) pp.mds[i][j] = fp_inv(fp_add(pts[i], pts[kT + j]));
+        return;
+    }
+}
+
+// ------------------------------------------------------- sparse rewrite
+namespace {
+using Mat = std::vector<std::vector<uint64_t>>;
+
+Mat matmul(const Mat &a, const Mat &b) {
+    size_t n = a.size(), m = b[0].size(), k = b.size();
+    Mat c(n, std::vector<uint64_t>(m, 0));
+    for (size_t i = 0; i < n; ++i)
+        for (size_t j = 0; j < m; ++j) {
+            uint64_t s = 0;
+            for (size_t l = 0; l < k; ++l) s = fp_add(s, fp_mul(a[i][l], b[l][j]));
+            c[i][j] = s;
+        }
+    return c;
+}
+
+// Solve A x = b over F_p (A square, invertible); returns false if singular.
+bool solve(Mat a, std::vector<uint64_t> b, std::vector<uint64_t> &x) {
+    const size_t n = a.size();
+    for (size_t col = 0; col < n; ++col) {
+        size_t piv = col;
+        while (piv < n && a[piv][col] == 0) ++piv;
+        if (piv == n) return false;
+        std::swap(a[piv], a[col]);
+        std::swap(b[piv], b[col]);
+        uint64_t inv = fp_inv(a[col][col]);
+        for (size_t j = col; j < n; ++j) a[col][j] = fp_mul(a[col][j], inv);
+        b[col] = fp_mul(b[col], inv);
+        for (size_t r = 0; r < n; ++r) {
+            if (r == col || a[r][col] == 0) continue;
+            uint64_t f = a[r][col];
+            for (size_t j = col; j < n; ++j) a[r][j] = fp_sub(a[r][j], fp_mul(f, a[col][j]));
+            b[r] = fp_sub(b[r], fp_mul(f, b[col]));
+        }
+    }
+    x = b;
+    return true;
+}
+}  // namespace
+
+bool derive_optimized(const PlainParams &pp, OptParams &op) {
+    const int first_part = kRF / 2, last_part = kRF / 2 + kRP - 1;
+    Mat M(kT, std::vector<uint64_t>(kT));
+    for (int i = 0; i < kT; ++i)
+        for (int j = 0; j < kT; ++j) M[i][j] = pp.mds[i][j];
+
+    // constants: forward carry of cells 1..11 through each partial round
+    std::vector<uint64_t> carry(kT, 0);  // constant still to be added before the next S-box
+    for (int i = 0; i < kT; ++i) carry[i] = pp.rc[first_part][i];
+    for (int r = first_part; r <= last_part; ++r) {
+        op.part_rc[r - first_part] = carry[0];
+        std::vector<uint64_t> rest(kT, 0);
+        for (int i = 1; i < kT; ++i) rest[i] = carry[i];
+        std::vector<uint64_t> next(kT, 0);
+        for (int i = 0; i < kT; ++i) {
+            uint64_t s = 0;
+            for (int j = 1; j < kT; ++j) s = fp_add(s, fp_mul(M[i][j], rest[j]));
+            next[i] = s;
+        }
+        for (int i = 0; i < kT; ++i) carry[i] = fp_add(next[i], pp.rc[r + 1][i]);
+    }
+    // full-round constants: rounds 0..3, then 26 (with the carried remainder), 27..29
+    for (int r = 0; r < first_part; ++r)
+        for (int i = 0; i < kT; ++i) op.full_rc[r][i] = pp.rc[r][i];
+    for (int i = 0; i < kT; ++i) op.full_rc[first_part][i] = carry[i];
+    for (int r = last_part + 2; r < kRounds; ++r)
+        for (int i = 0; i < kT; ++i) op.full_rc[r - kRP][i] = pp.rc[r][i];
+
+    // matrices: backwards factorisation N = A * diag(1, N_hat)
+    Mat N = M;
+    for (int r = last_part; r >= first_part; --r) {
+        const int q = r - first_part;
+        Mat Nhat_T(kT - 1, std::vector<uint64_t>(kT - 1));
+        for (int i = 1; i < kT; ++i)
+            for (int j = 1; j < kT; ++j) Nhat_T[j - 1][i - 1] = N[i][j];
+        std::vector<uint64_t> nrow(kT - 1), v;
+        for (int j = 1; j < kT; ++j) nrow[j - 1] = N[0][j];
+        if (!solve(Nhat_T, nrow, v)) return false;
+        op.part_v[q][0] = N[0][0];
+        for (int j = 1; j < kT; ++j) op.part_v[q][j] = v[j - 1];
+        for (int i = 1; i < kT; ++i) op.part_w[q][i - 1] = N[i][0];
+        Mat B(kT, std::vector<uint64_t>(kT, 0));
+        B[0][0] = 1;
+        for (int i = 1; i < kT; ++i)
+            for (int j = 1; j < kT; ++j) B[i][j] = N[i][j];
+        N = matmul(B, M);  // the previous round's matrix absorbs B
+    }
+    for (int i = 0; i < kT; ++i)
+        for (int j = 0; j < kT; ++j) {
+            op.mds[i][j] = pp.mds[i][j];
+            op.pre[i][j] = N[i][j];
+        }
+    return true;
+}
+
+}  // namespace host
+}  // namespace pg12

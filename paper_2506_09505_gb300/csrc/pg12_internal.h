@@ -1,0 +1,45 @@
+// Internal declarations shared by the host and device translation units of
+// the library (not part of the public ABI in include/pg12.h).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+namespace pg12 {
+
+constexpr uint64_t kP = 0xFFFFFFFF00000001ull;  // Eq. 1
+constexpr uint64_t kEps = 0xFFFFFFFFull;        // 2^64 mod p = 2^32 - 1
+constexpr int kT = 12;                          // state width (Sec. 2.4)
+constexpr int kRF = 8;                          // full rounds, 2 x HALF_FULL_ROUNDS
+constexpr int kRP = 22;                         // PARTIAL_ROUNDS (Alg. 1)
+constexpr int kRounds = kRF + kRP;
+constexpr int kRate = 8;                        // sponge chunk (Sec. 2.4)
+constexpr int kDigest = 4;
+
+// Plain-form parameter set: x <- M * S(x + rc[r]) for r = 0..29.
+struct PlainParams {
+    uint64_t rc[kRounds][kT];
+    uint64_t mds[kT][kT];
+};
+
+// Optimised form (Alg. 1 with MDSPartial), as the device consumes it.
+struct OptParams {
+    uint64_t full_rc[kRF][kT];    // rounds 0..3 then 26..29
+    uint64_t mds[kT][kT];         // dense matrix of full rounds 0..2, 26..29
+    uint64_t pre[kT][kT];         // dense transition matrix of full round 3
+    uint64_t part_rc[kRP];        // scalar into cell 0, per partial round
+    uint64_t part_v[kRP][kT];     // new_0 = sum_j v[j] x_j
+    uint64_t part_w[kRP][kT - 1]; // new_i = x_i + w[i-1] x_0
+};
+
+namespace host {
+uint64_t fp_add(uint64_t a, uint64_t b);
+uint64_t fp_sub(uint64_t a, uint64_t b);
+uint64_t fp_mul(uint64_t a, uint64_t b);
+uint64_t fp_pow(uint64_t a, uint64_t e);
+uint64_t fp_inv(uint64_t a);
+void generate_plain(PlainParams &pp);
+bool derive_optimized(const PlainParams &pp, OptParams &op);
+}  // namespace host
+
+}  // namespace pg12
