@@ -3,10 +3,11 @@
 // Values travel between operations as 64-bit "weak" representatives: any
 // word in [0, 2^64) standing for its residue mod p.  Only stored results are
 // made canonical (0 <= e < p, Sec. 2.4).  Products are formed from four
-// 32x32->64 partial products (IMAD.WIDE.U32) and folded with the identities
-// 2^64 = 2^32 - 1 and 2^96 = -1 (mod p) -- the special-prime reduction of
-// Alg. 2 and Eqs. 2-4, rewritten for 32-bit limbs so that no 64-bit
-// multiply is needed.
+// 32x32->64 partial products (IMAD.WIDE.U32 with a zero addend, so no
+// register pair has to be built for the addend) and summed column by column
+// in carry chains.  The 128-bit (or 160-bit) result is folded with
+// 2^64 = 2^32 - 1, 2^96 = -1 and 2^128 = -2^32 (mod p): the special-prime
+// reduction of Alg. 2 and Eqs. 2-4 on 32-bit limbs, with no 64-bit multiply.
 #pragma once
 #include <cstdint>
 
@@ -16,59 +17,76 @@ namespace dev {
 constexpr uint64_t P = 0xFFFFFFFF00000001ull;
 constexpr uint64_t EPS = 0xFFFFFFFFull;  // 2^64 mod p
 
+typedef unsigned __int128 u128;
+typedef __int128 s128;
+
 __device__ __forceinline__ uint32_t lo32(uint64_t x) { return (uint32_t)x; }
 __device__ __forceinline__ uint32_t hi32(uint64_t x) { return (uint32_t)(x >> 32); }
 
-// Full 128-bit product a*b = (hi, lo) from four IMAD.WIDE.U32.
-__device__ __forceinline__ void mul_full(uint64_t a, uint64_t b, uint64_t &lo, uint64_t &hi) {
+// The four partial products of a*b (each < 2^64).
+struct Partial {
+    uint64_t ll, lh, hl, hh;
+};
+
+__device__ __forceinline__ Partial partials(uint64_t a, uint64_t b) {
     const uint32_t a0 = lo32(a), a1 = hi32(a), b0 = lo32(b), b1 = hi32(b);
-    const uint64_t ll = (uint64_t)a0 * b0;
-    const uint64_t lh = (uint64_t)a0 * b1 + (ll >> 32);       // < 2^64
-    const uint64_t hl = (uint64_t)a1 * b0 + (uint64_t)lo32(lh); // < 2^64
-    hi = (uint64_t)a1 * b1 + (lh >> 32) + (hl >> 32);          // < 2^64
-    lo = (hl << 32) | (uint64_t)lo32(ll);
+    Partial q;
+    q.ll = (uint64_t)a0 * b0;
+    q.lh = (uint64_t)a0 * b1;
+    q.hl = (uint64_t)a1 * b0;
+    q.hh = (uint64_t)a1 * b1;
+    return q;
 }
 
-// a^2 from three partial products (the cross term is doubled).
-__device__ __forceinline__ void sqr_full(uint64_t a, uint64_t &lo, uint64_t &hi) {
+// (r3:r2:r1:r0) = ll + (lh + hl) * 2^32 + hh * 2^64, two carry chains.
+__device__ __forceinline__ u128 join(const Partial &q) {
+    uint32_t r0 = lo32(q.ll), r1, r2, r3;
+    asm("add.cc.u32 %0, %3, %4;\n\t"
+        "addc.cc.u32 %1, %5, %6;\n\t"
+        "addc.u32 %2, %7, 0;\n\t"
+        "add.cc.u32 %0, %0, %8;\n\t"
+        "addc.cc.u32 %1, %1, %9;\n\t"
+        "addc.u32 %2, %2, 0;"
+        : "=r"(r1), "=r"(r2), "=r"(r3)
+        : "r"(hi32(q.ll)), "r"(lo32(q.lh)), "r"(hi32(q.lh)), "r"(lo32(q.hh)), "r"(hi32(q.hh)),
+          "r"(lo32(q.hl)), "r"(hi32(q.hl)));
+    return ((u128)(((uint64_t)r3 << 32) | r2) << 64) | (((uint64_t)r1 << 32) | r0);
+}
+
+// a^2 = ll + 2 lh 2^32 + hh 2^64 from three partial products.
+__device__ __forceinline__ u128 sqr_full(uint64_t a) {
     const uint32_t a0 = lo32(a), a1 = hi32(a);
-    const uint64_t ll = (uint64_t)a0 * a0;
-    const uint64_t lh = (uint64_t)a0 * a1;
-    const uint64_t mid1 = lh + (ll >> 32);  // < 2^64
-    const uint64_t mid = mid1 + lh;         // 65-bit sum: keep the carry
-    const uint64_t carry = (mid < lh) ? (1ull << 32) : 0ull;
-    hi = (uint64_t)a1 * a1 + (mid >> 32) + carry;
-    lo = (mid << 32) | (uint64_t)lo32(ll);
+    const uint64_t ll = (uint64_t)a0 * a0, lh = (uint64_t)a0 * a1, hh = (uint64_t)a1 * a1;
+    uint32_t r1, r2, r3;
+    asm("add.cc.u32 %0, %3, %4;\n\t"
+        "addc.cc.u32 %1, %5, %6;\n\t"
+        "addc.u32 %2, %7, 0;\n\t"
+        "add.cc.u32 %0, %0, %4;\n\t"
+        "addc.cc.u32 %1, %1, %5;\n\t"
+        "addc.u32 %2, %2, 0;"
+        : "=r"(r1), "=r"(r2), "=r"(r3)
+        : "r"(hi32(ll)), "r"(lo32(lh)), "r"(hi32(lh)), "r"(lo32(hh)), "r"(hi32(hh)));
+    return ((u128)(((uint64_t)r3 << 32) | r2) << 64) | (((uint64_t)r1 << 32) | lo32(ll));
 }
 
-// 128-bit (hi, lo) -> weak 64-bit residue.
-// With hi = hh*2^32 + hl:  value = lo - hh + hl*(2^32 - 1)  (mod p).
-// A borrow out of lo - hh is worth -2^64 = -(2^32 - 1); a carry out of the
-// final sum is worth +(2^32 - 1); neither correction can wrap again.
-__device__ __forceinline__ uint64_t reduce128(uint64_t lo, uint64_t hi) {
-    const uint64_t hh = hi >> 32;
-    const uint64_t hl = hi & EPS;
-    uint64_t t0 = lo - hh;
-    if (lo < hh) t0 -= EPS;
-    const uint64_t t1 = (hl << 32) - hl;
-    uint64_t r = t0 + t1;
-    if (r < t1) r += EPS;
-    return r;
+// value = lo + hl 2^32 - hl - hh - k 2^32 (mod p) for hi = hh:hl and a small
+// extra k (the 2^128 limb of a lazy sum, 2^128 = -2^32).  The signed 128-bit
+// result t lies in (-2^37, 2^65); its top word is -1, 0 or 1 and is folded
+// back as +-(2^32 - 1).  Neither correction can wrap again.
+__device__ __forceinline__ uint64_t fold(uint64_t lo, uint64_t hi, uint32_t k) {
+    const uint64_t hl = hi & EPS, hh = hi >> 32;
+    const s128 t = (s128)lo + (s128)(hl << 32) - (s128)(hl + hh) - (s128)((uint64_t)k << 32);
+    const uint64_t top = (uint64_t)(t >> 64);
+    return (uint64_t)t + ((top << 32) - top);
 }
+
+__device__ __forceinline__ uint64_t reduce128(u128 r) { return fold((uint64_t)r, (uint64_t)(r >> 64), 0); }
 
 __device__ __forceinline__ uint64_t canon(uint64_t x) { return x >= P ? x - P : x; }
 
-__device__ __forceinline__ uint64_t mul(uint64_t a, uint64_t b) {
-    uint64_t lo, hi;
-    mul_full(a, b, lo, hi);
-    return reduce128(lo, hi);
-}
+__device__ __forceinline__ uint64_t mul(uint64_t a, uint64_t b) { return reduce128(join(partials(a, b))); }
 
-__device__ __forceinline__ uint64_t sqr(uint64_t a) {
-    uint64_t lo, hi;
-    sqr_full(a, lo, hi);
-    return reduce128(lo, hi);
-}
+__device__ __forceinline__ uint64_t sqr(uint64_t a) { return reduce128(sqr_full(a)); }
 
 // weak a + canonical c (c < p): at most one wrap, folded as +(2^32 - 1).
 __device__ __forceinline__ uint64_t add_canon(uint64_t a, uint64_t c) {
@@ -85,36 +103,55 @@ __device__ __forceinline__ uint64_t sbox(uint64_t x) {
     return mul(x4, x3);
 }
 
-// 160-bit accumulator for lazily reduced dot products: sum of up to 2^32
-// 128-bit products.
+// x + w*y as one 128-bit value (x added into the product), reduced once.
+__device__ __forceinline__ uint64_t mul_add(uint64_t w, uint64_t y, uint64_t x) {
+    u128 r = join(partials(w, y));
+    r += x;  // < 2^128: the product is below p * 2^64
+    return reduce128(r);
+}
+
+// Lazy dot-product accumulator.  The outer partial products (ll, hh) of a
+// term are one contiguous 128-bit value and go into a 160-bit sum; the two
+// middle products go into a separate 96-bit sum that is shifted in once at
+// the end.  Holds up to 2^32 terms.
 struct Acc {
-    uint64_t lo, hi;
-    uint32_t top;
+    uint32_t a0, a1, a2, a3, a4;
+    uint32_t m0, m1, m2;
 };
 
-__device__ __forceinline__ void acc_zero(Acc &a) { a.lo = 0; a.hi = 0; a.top = 0; }
-
-__device__ __forceinline__ void acc_add128(Acc &a, uint64_t plo, uint64_t phi) {
-    asm volatile("add.cc.u64 %0, %0, %3;\n\t"
-        "addc.cc.u64 %1, %1, %4;\n\t"
-        "addc.u32 %2, %2, 0;"
-        : "+l"(a.lo), "+l"(a.hi), "+r"(a.top)
-        : "l"(plo), "l"(phi));
+__device__ __forceinline__ void acc_zero(Acc &A) {
+    A.a0 = A.a1 = A.a2 = A.a3 = A.a4 = 0;
+    A.m0 = A.m1 = A.m2 = 0;
 }
 
-__device__ __forceinline__ void acc_mac(Acc &a, uint64_t x, uint64_t m) {
-    uint64_t plo, phi;
-    mul_full(x, m, plo, phi);
-    acc_add128(a, plo, phi);
+__device__ __forceinline__ void acc_mac(Acc &A, uint64_t x, uint64_t m) {
+    const Partial q = partials(x, m);
+    asm("add.cc.u32 %0, %0, %8;\n\t"
+        "addc.cc.u32 %1, %1, %9;\n\t"
+        "addc.cc.u32 %2, %2, %10;\n\t"
+        "addc.cc.u32 %3, %3, %11;\n\t"
+        "addc.u32 %4, %4, 0;\n\t"
+        "add.cc.u32 %5, %5, %12;\n\t"
+        "addc.cc.u32 %6, %6, %13;\n\t"
+        "addc.u32 %7, %7, 0;\n\t"
+        "add.cc.u32 %5, %5, %14;\n\t"
+        "addc.cc.u32 %6, %6, %15;\n\t"
+        "addc.u32 %7, %7, 0;"
+        : "+r"(A.a0), "+r"(A.a1), "+r"(A.a2), "+r"(A.a3), "+r"(A.a4), "+r"(A.m0), "+r"(A.m1), "+r"(A.m2)
+        : "r"(lo32(q.ll)), "r"(hi32(q.ll)), "r"(lo32(q.hh)), "r"(hi32(q.hh)), "r"(lo32(q.lh)),
+          "r"(hi32(q.lh)), "r"(lo32(q.hl)), "r"(hi32(q.hl)));
 }
 
-// 160-bit -> weak 64-bit: top * 2^128 = -top * 2^32 (mod p) since 2^96 = -1.
-__device__ __forceinline__ uint64_t acc_reduce(const Acc &a) {
-    const uint64_t r = reduce128(a.lo, a.hi);
-    const uint64_t t = (uint64_t)a.top << 32;
-    uint64_t u = r - t;
-    if (r < t) u -= EPS;  // the wrap added 2^64 = 2^32 - 1
-    return u;
+// sum -> weak 64-bit residue.
+__device__ __forceinline__ uint64_t acc_reduce(const Acc &A) {
+    uint32_t a1, a2, a3, a4;
+    asm("add.cc.u32 %0, %4, %8;\n\t"
+        "addc.cc.u32 %1, %5, %9;\n\t"
+        "addc.cc.u32 %2, %6, %10;\n\t"
+        "addc.u32 %3, %7, 0;"
+        : "=r"(a1), "=r"(a2), "=r"(a3), "=r"(a4)
+        : "r"(A.a1), "r"(A.a2), "r"(A.a3), "r"(A.a4), "r"(A.m0), "r"(A.m1), "r"(A.m2));
+    return fold(((uint64_t)a1 << 32) | A.a0, ((uint64_t)a3 << 32) | a2, a4);
 }
 
 }  // namespace dev

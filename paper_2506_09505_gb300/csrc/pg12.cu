@@ -25,31 +25,23 @@ namespace pg12 {
 namespace dev {
 
 // ------------------------------------------------------------- geometry
-constexpr int kBlock = 256;     // threads per Merkle block
-constexpr int kLeafTile = 256;  // rows per leaf tile
-constexpr int kNodeTile = 512;  // child nodes consumed per node tile
-constexpr int kTileOut = 32;    // outputs of a tile that is not the last one
-constexpr int kMaxStages = 12;
+constexpr int kBlock = 256;     // threads per Merkle block (8 independent warps)
+constexpr int kWarpNodes = 32;  // nodes of one level hashed by one warp task
+constexpr int kMaxLevels = 40;
 
-struct StagePlan {
-    uint32_t n_tiles;       // tiles in this stage
-    uint32_t in_per_tile;   // rows (stage 0) or child nodes per tile
-    uint32_t levels;        // tree levels written by one tile
-    uint32_t in_level;      // level of the child nodes (stages >= 1)
-    uint32_t counter_base;  // first arrival counter of this stage (stages >= 1)
-    uint32_t fan_in;        // child tiles per tile (stages >= 1)
-};
-
+// One tree of a build.  A "task" is 32 consecutive nodes of one level,
+// hashed by one warp (one node per lane).  Level l has ceil((N>>l)/32)
+// tasks; task u of level l >= 1 needs tasks 2u and 2u+1 of level l-1.
 struct TreePlan {
     const uint64_t *rows;
     uint64_t *nodes;
     uint64_t n_leaves;
     uint64_t width;
-    uint32_t n_stages;
+    uint32_t log_n;
     uint32_t leaf_task_begin;  // first global leaf-task index of this tree
     uint32_t counter_base;     // first arrival counter of this tree
     uint32_t vec16;            // rows can be read with 16-byte loads
-    StagePlan st[kMaxStages];
+    uint32_t level_counter[kMaxLevels];  // counter offset of level l's tasks (l >= 1)
 };
 
 __device__ __forceinline__ uint64_t level_off(uint64_t n, uint32_t level) {
@@ -85,136 +77,113 @@ __device__ __forceinline__ void load_chunk(const uint64_t *row, uint64_t w, uint
     }
 }
 
-// Overwrite-mode sponge over one row; digest is canonical.
-__device__ __forceinline__ void sponge_row(const uint64_t *row, uint64_t w, bool vec16,
-                                           uint64_t (&d)[kDigest]) {
-    uint64_t x[kT];
+// Overwrite-mode sponge over one row in the thread's state slot; returns
+// with the (weak) final state in the slot.
+template <int S>
+__device__ __forceinline__ void sponge_slot(const uint64_t *row, uint64_t w, bool vec16, uint64_t *slot) {
 #pragma unroll
-    for (int i = 0; i < kT; ++i) x[i] = 0;
+    for (int i = kRate; i < kT; ++i) slot[i * S] = 0;
     const uint64_t chunks = w == 0 ? 1 : (w + kRate - 1) / kRate;
-    uint64_t nxt[kRate];
-    load_chunk(row, w, 0, vec16, nxt);
     for (uint64_t c = 0; c < chunks; ++c) {
+        uint64_t ch[kRate];
+        load_chunk(row, w, c, vec16, ch);
 #pragma unroll
-        for (int i = 0; i < kRate; ++i) x[i] = nxt[i];
-        if (c + 1 < chunks) load_chunk(row, w, c + 1, vec16, nxt);
-        permute(x);
+        for (int i = 0; i < kRate; ++i) slot[i * S] = ch[i];
+        permute_slot<S>(slot);
     }
-#pragma unroll
-    for (int i = 0; i < kDigest; ++i) d[i] = canon(x[i]);
 }
 
 // ------------------------------------------------------------- kernels
-__global__ void __launch_bounds__(128) k_permute(uint64_t *__restrict__ st, uint64_t n, int vec16) {
+constexpr int kSmallBlock = 128;
+
+__global__ void __launch_bounds__(kSmallBlock) k_permute(uint64_t *__restrict__ st, uint64_t n, int vec16) {
+    __shared__ uint64_t slots[kT * kSmallBlock];
+    uint64_t *slot = slots + threadIdx.x;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
         uint64_t *p = st + kT * k;
-        uint64_t x[kT];
         if (vec16) {
 #pragma unroll
-            for (int i = 0; i < kT; i += 2) ld2_nc(p + i, x[i], x[i + 1]);
+            for (int i = 0; i < kT; i += 2) {
+                uint64_t a, b;
+                ld2_nc(p + i, a, b);
+                slot[i * kSmallBlock] = a;
+                slot[(i + 1) * kSmallBlock] = b;
+            }
         } else {
 #pragma unroll
-            for (int i = 0; i < kT; ++i) x[i] = p[i];
+            for (int i = 0; i < kT; ++i) slot[i * kSmallBlock] = p[i];
         }
-        permute(x);
+        permute_slot<kSmallBlock>(slot);
         if (vec16) {
 #pragma unroll
-            for (int i = 0; i < kT; i += 2) st2(p + i, canon(x[i]), canon(x[i + 1]));
+            for (int i = 0; i < kT; i += 2) st2(p + i, canon(slot[i * kSmallBlock]), canon(slot[(i + 1) * kSmallBlock]));
         } else {
 #pragma unroll
-            for (int i = 0; i < kT; ++i) p[i] = canon(x[i]);
+            for (int i = 0; i < kT; ++i) p[i] = canon(slot[i * kSmallBlock]);
         }
     }
 }
 
-__global__ void __launch_bounds__(128) k_hash_rows(const uint64_t *__restrict__ rows, uint64_t n,
-                                                   uint64_t w, int vec16, uint64_t *__restrict__ out) {
+__global__ void __launch_bounds__(kSmallBlock) k_hash_rows(const uint64_t *__restrict__ rows, uint64_t n,
+                                                           uint64_t w, int vec16, uint64_t *__restrict__ out) {
+    __shared__ uint64_t slots[kT * kSmallBlock];
+    uint64_t *slot = slots + threadIdx.x;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
-        uint64_t d[kDigest];
-        sponge_row(rows + r * w, w, vec16 != 0, d);
-        st2(out + kDigest * r, d[0], d[1]);
-        st2(out + kDigest * r + 2, d[2], d[3]);
+        sponge_slot<kSmallBlock>(rows + r * w, w, vec16 != 0, slot);
+        st2(out + kDigest * r, canon(slot[0]), canon(slot[kSmallBlock]));
+        st2(out + kDigest * r + 2, canon(slot[2 * kSmallBlock]), canon(slot[3 * kSmallBlock]));
     }
 }
 
-// One tile: its first level from rows (stage 0) or from child nodes in
-// global memory, then the following levels from shared memory.  Every
-// permutation of the tile goes through a single call site (several inlined
-// copies of the permutation would multiply its register footprint).
-__device__ void run_tile(const TreePlan &tp, uint32_t s, uint32_t tile,
-                         uint64_t (&buf)[2][kBlock][kDigest]) {
-    const int t = threadIdx.x;
-    const StagePlan st = tp.st[s];
+// One warp task: lane i of task u at level l hashes node 32u+i of that level
+// -- a row through the sponge at level 0, else the pair of children at
+// level l-1 -- in the lane's shared-memory state slot.
+__device__ __forceinline__ void run_warp_task(const TreePlan &tp, uint32_t level, uint64_t u, int lane,
+                                              uint64_t *slot) {
     const uint64_t n = tp.n_leaves;
-    const uint64_t w = tp.width;
-    const bool vec16 = tp.vec16 != 0;
-    // first level: stage 0 hashes rows, later stages hash child pairs
-    uint32_t cnt = s == 0 ? st.in_per_tile : st.in_per_tile / 2;
-    uint32_t level = s == 0 ? 0 : st.in_level + 1;
-    const uint64_t row_chunks = w == 0 ? 1 : (w + kRate - 1) / kRate;
-    int b = 0;
-    for (uint32_t k = 0; k < st.levels; ++k) {
-        if (k > 0) {
-            __syncthreads();
-            cnt /= 2;
-            ++level;
+    const uint64_t count = n >> level;
+    const uint64_t i = u * kWarpNodes + lane;
+    if (i >= count) return;
+    if (level == 0) {
+        sponge_slot<kBlock>(tp.rows + i * tp.width, tp.width, tp.vec16 != 0, slot);
+    } else {
+        const uint64_t *kids = tp.nodes + kDigest * (level_off(n, level - 1) + 2 * i);
+#pragma unroll
+        for (int k = 0; k < 2 * kDigest; k += 2) {
+            uint64_t a, b;
+            ld2_cg(kids + k, a, b);
+            slot[k * kBlock] = a;
+            slot[(k + 1) * kBlock] = b;
         }
-        if (t < (int)cnt) {
-            const bool sponge = (s == 0 && k == 0);
-            const uint64_t nperm = sponge ? row_chunks : 1;
-            const uint64_t *row = tp.rows + ((uint64_t)tile * cnt + t) * w;
-            const uint64_t *kids = nullptr;
-            if (s != 0 && k == 0)
-                kids = tp.nodes + kDigest * (level_off(n, st.in_level) + (uint64_t)tile * st.in_per_tile + 2 * t);
-            uint64_t x[kT];
 #pragma unroll
-            for (int i = 0; i < kT; ++i) x[i] = 0;
-            for (uint64_t c = 0; c < nperm; ++c) {
-                if (sponge) {
-                    uint64_t ch[kRate];
-                    load_chunk(row, w, c, vec16, ch);
-#pragma unroll
-                    for (int i = 0; i < kRate; ++i) x[i] = ch[i];
-                } else if (k == 0) {
-#pragma unroll
-                    for (int i = 0; i < 2 * kDigest; i += 2) ld2_cg(kids + i, x[i], x[i + 1]);
-                } else {
-#pragma unroll
-                    for (int i = 0; i < kDigest; ++i) {
-                        x[i] = buf[b][2 * t][i];
-                        x[kDigest + i] = buf[b][2 * t + 1][i];
-                    }
-                }
-                permute(x);
-            }
-            uint64_t d[kDigest];
-#pragma unroll
-            for (int i = 0; i < kDigest; ++i) d[i] = canon(x[i]);
-            uint64_t *dst = tp.nodes + kDigest * (level_off(n, level) + (uint64_t)tile * cnt + t);
-            st2(dst, d[0], d[1]);
-            st2(dst + 2, d[2], d[3]);
-            const int ob = k == 0 ? 0 : (b ^ 1);
-#pragma unroll
-            for (int i = 0; i < kDigest; ++i) buf[ob][t][i] = d[i];
-        }
-        if (k > 0) b ^= 1;
+        for (int k = 2 * kDigest; k < kT; ++k) slot[k * kBlock] = 0;
+        permute_slot<kBlock>(slot);
     }
-    __syncthreads();
+    uint64_t *dst = tp.nodes + kDigest * (level_off(n, level) + i);
+    st2(dst, canon(slot[0]), canon(slot[kBlock]));
+    st2(dst + 2, canon(slot[2 * kBlock]), canon(slot[3 * kBlock]));
 }
 
+// Persistent Merkle kernel: every warp pulls leaf tasks from a global
+// counter (in order, so sibling subtrees finish close together), hashes
+// them, and announces each finished task to its parent's arrival counter.
+// The warp that brings a parent's count to two (its second child) builds
+// the parent and keeps climbing; the first arriver goes back for a new leaf
+// task.  Levels with at most 32 nodes have a single task and are climbed
+// without counters.  No block-wide barrier and no waiting anywhere.
 __global__ void __launch_bounds__(kBlock) k_merkle(const TreePlan *__restrict__ plans, uint32_t n_trees,
                                                    uint32_t total_tasks, uint32_t *__restrict__ counters,
                                                    uint32_t *__restrict__ next_task) {
-    __shared__ uint64_t buf[2][kBlock][kDigest];
-    __shared__ uint32_t s_task, s_go;
-    const int t = threadIdx.x;
+    __shared__ uint64_t slots[kT * kBlock];
+    uint64_t *slot = slots + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const unsigned full = 0xFFFFFFFFu;
     for (;;) {
-        if (t == 0) s_task = atomicAdd(next_task, 1u);
-        __syncthreads();
-        const uint32_t task = s_task;
-        __syncthreads();
+        uint32_t task = 0;
+        if (lane == 0) task = atomicAdd(next_task, 1u);
+        task = __shfl_sync(full, task, 0);
         if (task >= total_tasks) return;
         uint32_t lo = 0, hi = n_trees - 1;
         while (lo < hi) {
@@ -223,20 +192,26 @@ __global__ void __launch_bounds__(kBlock) k_merkle(const TreePlan *__restrict__ 
             else hi = mid - 1;
         }
         const TreePlan &tp = plans[lo];
-        uint32_t tile = task - tp.leaf_task_begin;
-        run_tile(tp, 0, tile, buf);
-        for (uint32_t s = 1; s < tp.n_stages; ++s) {
-            const uint32_t fan = tp.st[s].fan_in;
-            const uint32_t parent = tile / fan;
-            __threadfence();  // this tile's node writes before the arrival
-            __syncthreads();
-            if (t == 0)
-                s_go = (atomicAdd(&counters[tp.counter_base + tp.st[s].counter_base + parent], 1u) == fan - 1);
-            __syncthreads();
-            if (!s_go) break;
-            __threadfence();  // the siblings' writes are visible from here on
-            tile = parent;
-            run_tile(tp, s, tile, buf);
+        const uint64_t n = tp.n_leaves;
+        const uint32_t log_n = tp.log_n;
+        uint64_t u = task - tp.leaf_task_begin;
+        run_warp_task(tp, 0, u, lane, slot);
+        for (uint32_t level = 1; level <= log_n; ++level) {
+            const uint64_t below = n >> (level - 1);
+            if (below > (uint64_t)kWarpNodes) {
+                // two child tasks: only the second to finish continues
+                __threadfence();
+                __syncwarp();
+                uint32_t old = 0;
+                if (lane == 0) old = atomicAdd(&counters[tp.counter_base + tp.level_counter[level] + (u >> 1)], 1u);
+                old = __shfl_sync(full, old, 0);
+                if (old == 0) break;
+                __threadfence();
+            } else {
+                __syncwarp();
+            }
+            u >>= 1;
+            run_warp_task(tp, level, u, lane, slot);
         }
     }
 }
@@ -295,50 +270,28 @@ uint32_t log2u(uint64_t x) {
     return l;
 }
 
-// Stage geometry of one tree (see k_merkle).  Returns false if the tree
-// needs more stages than the plan holds.
-bool plan_tree(dev::TreePlan &tp, const uint64_t *rows, uint64_t n, uint64_t w, uint64_t *nodes,
-               uint32_t leaf_task_begin, uint32_t counter_base, uint32_t &n_counters) {
+// Task geometry of one tree (see k_merkle).  n_counters receives the
+// number of arrival counters the tree needs; returns the leaf-task count.
+uint32_t plan_tree(dev::TreePlan &tp, const uint64_t *rows, uint64_t n, uint64_t w, uint64_t *nodes,
+                   uint32_t leaf_task_begin, uint32_t counter_base, uint32_t &n_counters) {
     tp.rows = rows;
     tp.nodes = nodes;
     tp.n_leaves = n;
     tp.width = w;
+    tp.log_n = log2u(n);
     tp.leaf_task_begin = leaf_task_begin;
     tp.counter_base = counter_base;
     tp.vec16 = ((w % 2) == 0 && (reinterpret_cast<uintptr_t>(rows) % 16) == 0) ? 1u : 0u;
     n_counters = 0;
-    uint32_t s = 0;
-    // stage 0: leaf tiles
-    {
-        dev::StagePlan &st = tp.st[0];
-        st.in_per_tile = (uint32_t)(n < (uint64_t)dev::kLeafTile ? n : dev::kLeafTile);
-        st.n_tiles = (uint32_t)(n / st.in_per_tile);
-        st.in_level = 0;
-        st.counter_base = 0;
-        st.fan_in = 0;
-        st.levels = st.n_tiles == 1 ? log2u(st.in_per_tile) + 1 : log2u(st.in_per_tile / dev::kTileOut) + 1;
+    for (uint32_t l = 0; l < (uint32_t)dev::kMaxLevels; ++l) tp.level_counter[l] = 0;
+    for (uint32_t l = 1; l <= tp.log_n; ++l) {
+        const uint64_t below = n >> (l - 1);
+        if (below > (uint64_t)dev::kWarpNodes) {
+            tp.level_counter[l] = n_counters;
+            n_counters += (uint32_t)(((n >> l) + dev::kWarpNodes - 1) / dev::kWarpNodes);
+        }
     }
-    uint64_t out_total = (uint64_t)tp.st[0].n_tiles * (tp.st[0].in_per_tile >> (tp.st[0].levels - 1));
-    uint32_t out_level = tp.st[0].levels - 1;
-    uint32_t prev_out = tp.st[0].in_per_tile >> (tp.st[0].levels - 1);
-    s = 1;
-    while (tp.st[s - 1].n_tiles > 1) {
-        if (s >= (uint32_t)dev::kMaxStages) return false;
-        dev::StagePlan &st = tp.st[s];
-        st.in_per_tile = (uint32_t)(out_total < (uint64_t)dev::kNodeTile ? out_total : dev::kNodeTile);
-        st.n_tiles = (uint32_t)(out_total / st.in_per_tile);
-        st.in_level = out_level;
-        st.fan_in = st.in_per_tile / prev_out;
-        st.counter_base = n_counters;
-        n_counters += st.n_tiles;
-        st.levels = st.n_tiles == 1 ? log2u(st.in_per_tile) : log2u(st.in_per_tile / dev::kTileOut);
-        prev_out = st.in_per_tile >> st.levels;
-        out_total = (uint64_t)st.n_tiles * prev_out;
-        out_level = st.in_level + st.levels;
-        ++s;
-    }
-    tp.n_stages = s;
-    return true;
+    return (uint32_t)((n + dev::kWarpNodes - 1) / dev::kWarpNodes);
 }
 
 cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
@@ -393,10 +346,14 @@ pg_status pg_init(int device, const char *params_path) {
     PG_CUDA(cudaGetDeviceCount(&ndev));
     if (device < 0 || device >= ndev) return fail(PG_ERR_INVALID_ARG, "device %d out of range (%d)", device, ndev);
     PG_CUDA(cudaSetDevice(device));
-    PG_CUDA(cudaMemcpyToSymbol(dev::c_opt, &g.opt, sizeof(OptParams)));
+    {
+        dev::DevConsts dc;
+        dev::make_dev_consts(g.opt, dc);
+        PG_CUDA(cudaMemcpyToSymbol(dev::c_dev, &dc, sizeof(dc)));
+    }
     PG_CUDA(cudaDeviceGetAttribute(&g.sms, cudaDevAttrMultiProcessorCount, device));
     PG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g.merkle_blocks_per_sm, dev::k_merkle, dev::kBlock, 0));
-    PG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g.permute_blocks_per_sm, dev::k_permute, 128, 0));
+    PG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g.permute_blocks_per_sm, dev::k_permute, dev::kSmallBlock, 0));
     if (g.merkle_blocks_per_sm < 1 || g.permute_blocks_per_sm < 1)
         return fail(PG_ERR_CUDA, "kernels cannot be resident (occupancy 0)");
     void *ws = nullptr;
@@ -459,15 +416,14 @@ pg_status pg_merkle_build(const uint64_t *rows, size_t n_leaves, size_t width, u
     if (!rows || !nodes) return fail(PG_ERR_INVALID_ARG, "rows or nodes is NULL");
     if (width == 0) return fail(PG_ERR_INVALID_ARG, "width must be >= 1");
     if (!is_pow2(n_leaves)) return fail(PG_ERR_NOT_POW2, "n_leaves=%zu is not a power of two", n_leaves);
-    if (n_leaves > (1ull << 31)) return fail(PG_ERR_INVALID_ARG, "n_leaves=%zu above 2^31", n_leaves);
+    if (n_leaves > (1ull << 34)) return fail(PG_ERR_INVALID_ARG, "n_leaves=%zu above 2^34", n_leaves);
     if (reinterpret_cast<uintptr_t>(rows) % 8) return fail(PG_ERR_INVALID_ARG, "rows not 8-byte aligned");
     if (reinterpret_cast<uintptr_t>(nodes) % 16) return fail(PG_ERR_INVALID_ARG, "nodes not 16-byte aligned");
     dev::TreePlan tp;
     std::memset(&tp, 0, sizeof tp);
     uint32_t n_counters = 0;
-    if (!plan_tree(tp, rows, n_leaves, width, nodes, 0, 0, n_counters))
-        return fail(PG_ERR_INVALID_ARG, "tree needs too many stages");
-    const size_t counter_bytes = sizeof(uint32_t) * (1 + n_counters);
+    const uint32_t tasks = plan_tree(tp, rows, n_leaves, width, nodes, 0, 0, n_counters);
+    const size_t counter_bytes = sizeof(uint32_t) * (1 + (size_t)n_counters);
     if (sizeof(tp) > kPlanBytes || counter_bytes > g.ws_bytes - kPlanBytes)
         return fail(PG_ERR_OOM, "workspace too small for %zu leaves", n_leaves);
     cudaStream_t st = as_stream(stream);
@@ -475,9 +431,10 @@ pg_status pg_merkle_build(const uint64_t *rows, size_t n_leaves, size_t width, u
     auto *d_counters = reinterpret_cast<uint32_t *>(g.ws + kPlanBytes);
     PG_CUDA(cudaMemcpyAsync(d_plan, &tp, sizeof tp, cudaMemcpyHostToDevice, st));
     PG_CUDA(cudaMemsetAsync(d_counters, 0, counter_bytes, st));
-    const uint32_t tasks = tp.st[0].n_tiles;
+    const uint32_t warps_per_block = dev::kBlock / 32;
+    const uint32_t want = (tasks + warps_per_block - 1) / warps_per_block;
     const uint32_t cap = (uint32_t)(g.sms * g.merkle_blocks_per_sm);
-    const unsigned grid = tasks < cap ? tasks : cap;
+    const unsigned grid = want < cap ? want : cap;
     dev::k_merkle<<<grid, dev::kBlock, 0, st>>>(d_plan, 1u, tasks, d_counters + 1, d_counters);
     PG_CUDA(cudaGetLastError());
     if (root_out) {

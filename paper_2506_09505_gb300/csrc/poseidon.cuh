@@ -1,15 +1,23 @@
 // Device Poseidon-12 permutation, one thread per state (Alg. 1).
 //
-// The state lives in twelve 64-bit registers.  Round structure (Alg. 1,
-// HALF_FULL_ROUNDS = 4, PARTIAL_ROUNDS = 22) in the optimised form whose
-// constants the host derives from (C, M):
+// Round structure (Alg. 1, HALF_FULL_ROUNDS = 4, PARTIAL_ROUNDS = 22) in the
+// optimised form whose constants the host derives from (C, M):
 //   full rounds 0..3   : x += c_r; x = x^7 (all cells); x = M x  (round 3 uses
 //                        the transition matrix instead of M)
 //   partial rounds     : x_0 += k_q; x_0 = x_0^7; MDSPartial:
 //                        new_0 = <v_q, x>, new_i = x_i + w_q[i-1] * x_0
 //   full rounds 26..29 : x += c_r; x = x^7; x = M x
-// Dense matrix rows are accumulated lazily: twelve 128-bit products summed
-// in 160 bits and reduced once per output cell.
+//
+// Code shape.  The fully unrolled permutation is ~100 KB of SASS; when the
+// warps of an SM sit in different rounds it no longer fits the instruction
+// caches.  So every phase is a short loop: the twelve state words live in
+// the thread's own shared-memory slot (element i at slot[i * STRIDE], so a
+// warp's accesses are consecutive words) between phases, the S-box phase
+// walks the slot two cells at a time, and the dense phase keeps the twelve
+// inputs in registers while it loops over output rows, fetching each row's
+// constants with uniform loads and storing each output straight back to
+// the slot.  Dense rows are accumulated lazily (twelve 128-bit products,
+// one reduction per output cell).
 #pragma once
 #include "field.cuh"
 #include "pg12_internal.h"
@@ -17,97 +25,90 @@
 namespace pg12 {
 namespace dev {
 
-// Constants of the optimised form (one copy per translation unit that
-// includes this header; filled by pg_init via cudaMemcpyToSymbol).
-__constant__ OptParams c_opt;
+// Device copy of the optimised constants, laid out for uniform loads.
+struct DevConsts {
+    uint64_t full_rc[kRF][kT];
+    uint64_t mat[2][kT][kT];  // [0] = M, [1] = transition matrix of round 3
+    uint64_t part_rc[kRP];
+    uint64_t part_v[kRP][kT];
+    uint64_t part_w[kRP][kT];  // entry 0 unused (keeps rows 16-byte aligned)
+};
 
-// y = N x for a dense 12x12 matrix held in constant memory.
-__device__ __forceinline__ void dense_layer(uint64_t (&x)[kT], const uint64_t (&n)[kT][kT]) {
-    uint64_t y[kT];
+// One copy per translation unit that includes this header; filled by
+// upload_constants() via cudaMemcpyToSymbol.
+__constant__ __align__(16) DevConsts c_dev;
+
+inline void make_dev_consts(const OptParams &op, DevConsts &dc) {
+    for (int r = 0; r < kRF; ++r)
+        for (int i = 0; i < kT; ++i) dc.full_rc[r][i] = op.full_rc[r][i];
+    for (int i = 0; i < kT; ++i)
+        for (int j = 0; j < kT; ++j) {
+            dc.mat[0][i][j] = op.mds[i][j];
+            dc.mat[1][i][j] = op.pre[i][j];
+        }
+    for (int q = 0; q < kRP; ++q) {
+        dc.part_rc[q] = op.part_rc[q];
+        for (int j = 0; j < kT; ++j) dc.part_v[q][j] = op.part_v[q][j];
+        dc.part_w[q][0] = 0;
+        for (int i = 1; i < kT; ++i) dc.part_w[q][i] = op.part_w[q][i - 1];
+    }
+}
+
+template <int S>
+__device__ __forceinline__ void sbox_phase(uint64_t *slot, int r) {
+#pragma unroll 1
+    for (int i = 0; i < kT; i += 2) {
+        const uint64_t a = add_canon(slot[i * S], c_dev.full_rc[r][i]);
+        const uint64_t b = add_canon(slot[(i + 1) * S], c_dev.full_rc[r][i + 1]);
+        slot[i * S] = sbox(a);
+        slot[(i + 1) * S] = sbox(b);
+    }
+}
+
+template <int S>
+__device__ __forceinline__ void dense_phase(uint64_t *slot, int m) {
+    uint64_t x[kT];
 #pragma unroll
+    for (int j = 0; j < kT; ++j) x[j] = slot[j * S];
+#pragma unroll 1
     for (int i = 0; i < kT; ++i) {
-        Acc a;
-        acc_zero(a);
+        Acc A;
+        acc_zero(A);
 #pragma unroll
-        for (int j = 0; j < kT; ++j) acc_mac(a, x[j], n[i][j]);
-        y[i] = acc_reduce(a);
+        for (int j = 0; j < kT; ++j) acc_mac(A, x[j], c_dev.mat[m][i][j]);
+        slot[i * S] = acc_reduce(A);
+    }
+}
+
+template <int S>
+__device__ __forceinline__ void partial_phase(uint64_t *slot) {
+    uint64_t x[kT];
+#pragma unroll
+    for (int j = 0; j < kT; ++j) x[j] = slot[j * S];
+#pragma unroll 1
+    for (int q = 0; q < kRP; ++q) {
+        const uint64_t x0 = sbox(add_canon(x[0], c_dev.part_rc[q]));
+        Acc A;
+        acc_zero(A);
+        acc_mac(A, x0, c_dev.part_v[q][0]);
+#pragma unroll
+        for (int j = 1; j < kT; ++j) acc_mac(A, x[j], c_dev.part_v[q][j]);
+#pragma unroll
+        for (int i = 1; i < kT; ++i) x[i] = mul_add(c_dev.part_w[q][i], x0, x[i]);
+        x[0] = acc_reduce(A);
     }
 #pragma unroll
-    for (int i = 0; i < kT; ++i) x[i] = y[i];
+    for (int j = 0; j < kT; ++j) slot[j * S] = x[j];
 }
 
-__device__ __forceinline__ void full_round(uint64_t (&x)[kT], const uint64_t (&rc)[kT],
-                                           const uint64_t (&n)[kT][kT]) {
-#pragma unroll
-    for (int i = 0; i < kT; ++i) x[i] = sbox(add_canon(x[i], rc[i]));
-    dense_layer(x, n);
-}
-
-__device__ __forceinline__ void partial_round(uint64_t (&x)[kT], int q) {
-    const uint64_t x0 = sbox(add_canon(x[0], c_opt.part_rc[q]));
-    Acc a;
-    acc_zero(a);
-    acc_mac(a, x0, c_opt.part_v[q][0]);
-#pragma unroll
-    for (int j = 1; j < kT; ++j) acc_mac(a, x[j], c_opt.part_v[q][j]);
-#pragma unroll
-    for (int i = 1; i < kT; ++i) {
-        uint64_t lo, hi;
-        mul_full(x0, c_opt.part_w[q][i - 1], lo, hi);
-        // add x_i into the 128-bit product before the single reduction
-        asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, 0;" : "+l"(lo), "+l"(hi) : "l"(x[i]));
-        x[i] = reduce128(lo, hi);
-    }
-    x[0] = acc_reduce(a);
-}
-
-// y = N x for a dense matrix addressed at run time (entries fetched with
-// uniform constant loads instead of constant-bank operands).
-__device__ __forceinline__ void dense_layer_rt(uint64_t (&x)[kT], const uint64_t *n) {
-    uint64_t y[kT];
-#pragma unroll
-    for (int i = 0; i < kT; ++i) {
-        Acc a;
-        acc_zero(a);
-#pragma unroll
-        for (int j = 0; j < kT; ++j) acc_mac(a, x[j], n[i * kT + j]);
-        y[i] = acc_reduce(a);
-    }
-#pragma unroll
-    for (int i = 0; i < kT; ++i) x[i] = y[i];
-}
-
-// Code shapes of the permutation (all compute the same map):
-//   kShapeCbank  one loop over the 8 full rounds; the dense layer is
-//                instantiated twice (M and the transition matrix) so that
-//                every matrix entry is a constant-bank operand;
-//   kShapeRt     one loop, one dense layer whose matrix is picked per round
-//                (fewer registers, extra constant loads).
-// A separate inlined copy per round group makes ptxas hoist constants
-// across the copies and spill, so the rounds are always one loop.
-enum PermShape { kShapeCbank = 0, kShapeRt = 1 };
-
-template <int SHAPE = kShapeCbank>
-__device__ __forceinline__ void permute(uint64_t (&x)[kT]) {
+// The permutation on the state in `slot` (weak words in, weak words out).
+template <int S>
+__device__ __forceinline__ void permute_slot(uint64_t *slot) {
 #pragma unroll 1
     for (int r = 0; r < kRF; ++r) {
-#pragma unroll
-        for (int i = 0; i < kT; ++i) x[i] = sbox(add_canon(x[i], c_opt.full_rc[r][i]));
-        if (SHAPE == kShapeRt) {
-            dense_layer_rt(x, r == kRF / 2 - 1 ? &c_opt.pre[0][0] : &c_opt.mds[0][0]);
-            if (r == kRF / 2 - 1) {
-#pragma unroll 1
-                for (int q = 0; q < kRP; ++q) partial_round(x, q);
-            }
-        } else {
-            if (r == kRF / 2 - 1) {
-                dense_layer(x, c_opt.pre);
-#pragma unroll 1
-                for (int q = 0; q < kRP; ++q) partial_round(x, q);
-            } else {
-                dense_layer(x, c_opt.mds);
-            }
-        }
+        sbox_phase<S>(slot, r);
+        dense_phase<S>(slot, r == kRF / 2 - 1 ? 1 : 0);
+        if (r == kRF / 2 - 1) partial_phase<S>(slot);
     }
 }
 
