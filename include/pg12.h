@@ -133,6 +133,30 @@ pg_status pg_hash_rows(const uint64_t *rows, size_t n_rows, size_t width, uint64
 pg_status pg_merkle_build(const uint64_t *rows, size_t n_leaves, size_t width, uint64_t *nodes,
                           uint64_t *root_out, void *stream);
 
+/*
+ * pg_merkle_build_noalloc -- the same tree as pg_merkle_build (identical
+ * output), for callers that cannot allocate device memory: code whose
+ * allocator forbids cudaMalloc, or a host process that may only use the
+ * buffers it was handed.  The paper has no counterpart; it is a property of
+ * this library's interface, not of the method.
+ *   rows, n_leaves, width, nodes  as for pg_merkle_build (caller-owned);
+ *                                 n_leaves must be at most 2^22, otherwise
+ *                                 PG_ERR_INVALID_ARG with a message naming
+ *                                 the limit.
+ *   stream                        cudaStream_t as void* (NULL = default).
+ * Allocates nothing and does not need pg_init().  Its scratch (the arrival
+ * counters of the build, 512 KiB) is a file-scope __device__ array that every
+ * GPU loading the library holds until process exit.  The first call on a
+ * device performs that device's set-up (uploads the constant tables and
+ * looks up the array's device address) with the device current; make that
+ * first call before any stream capture.  All calls share the one array,
+ * which keeps the previous call's contents (each call clears what it uses):
+ * calls that overlap on the GPU race and must be serialised by the caller.
+ * Asynchronous on `stream`; no root is returned (read it from nodes).
+ */
+pg_status pg_merkle_build_noalloc(const uint64_t *rows, size_t n_leaves, size_t width, uint64_t *nodes,
+                                  void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -216,6 +216,50 @@ __global__ void __launch_bounds__(kBlock) k_merkle(const TreePlan *__restrict__ 
     }
 }
 
+// ---------------------------------------------------- allocation-free build
+// For callers that cannot allocate device memory (for example code running
+// under an allocator that forbids cudaMalloc, or inside a host process that
+// only owns the buffers it was handed): the arrival counters live in this
+// file-scope array instead of the pg_init() workspace, and the tree plan is
+// passed by value as a kernel argument.  Every GPU that loads the library
+// holds the array (512 KiB) until the process exits.
+constexpr uint64_t kNoAllocMaxLeaves = 1ull << 22;
+constexpr size_t kNoAllocWords = (size_t)(kNoAllocMaxLeaves / kWarpNodes);  // task counter + arrival counters
+static __device__ __align__(256) uint32_t g_noalloc_scratch[kNoAllocWords];
+
+__global__ void __launch_bounds__(kBlock) k_merkle_single(const TreePlan tp, uint32_t total_tasks,
+                                                          uint32_t *__restrict__ counters,
+                                                          uint32_t *__restrict__ next_task) {
+    __shared__ uint64_t slots[kT * kBlock];
+    uint64_t *slot = slots + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const unsigned full = 0xFFFFFFFFu;
+    const uint64_t n = tp.n_leaves;
+    for (;;) {
+        uint32_t task = 0;
+        if (lane == 0) task = atomicAdd(next_task, 1u);
+        task = __shfl_sync(full, task, 0);
+        if (task >= total_tasks) return;
+        uint64_t u = task;
+        run_warp_task(tp, 0, u, lane, slot);
+        for (uint32_t level = 1; level <= tp.log_n; ++level) {
+            if ((n >> (level - 1)) > (uint64_t)kWarpNodes) {
+                __threadfence();
+                __syncwarp();
+                uint32_t old = 0;
+                if (lane == 0) old = atomicAdd(&counters[tp.level_counter[level] + (u >> 1)], 1u);
+                old = __shfl_sync(full, old, 0);
+                if (old == 0) break;
+                __threadfence();
+            } else {
+                __syncwarp();
+            }
+            u >>= 1;
+            run_warp_task(tp, level, u, lane, slot);
+        }
+    }
+}
+
 }  // namespace dev
 
 // ================================================================ host side
@@ -441,6 +485,65 @@ pg_status pg_merkle_build(const uint64_t *rows, size_t n_leaves, size_t width, u
         PG_CUDA(cudaMemcpyAsync(root_out, nodes + 4 * (2 * n_leaves - 2), 32, cudaMemcpyDeviceToHost, st));
         PG_CUDA(cudaStreamSynchronize(st));
     }
+    return PG_OK;
+}
+
+// Allocation-free variant of pg_merkle_build (declared in include/pg12.h).
+// Its first call on a device does that device's set-up, with the device
+// current: it uploads the constant tables (cudaMemcpyToSymbol) and resolves
+// the device address of g_noalloc_scratch once with cudaGetSymbolAddress --
+// in host code the array's name is only a host-side stand-in and must never
+// be handed to a kernel.  Make that first call before any stream capture.
+pg_status pg_merkle_build_noalloc(const uint64_t *rows, size_t n_leaves, size_t width, uint64_t *nodes,
+                                  void *stream) {
+    constexpr int kMaxDevices = 64;
+    static uint32_t *scratch_ptr[kMaxDevices];
+    static int blocks_per_sm[kMaxDevices];
+    static int sm_count[kMaxDevices];
+    if (!rows || !nodes) return fail(PG_ERR_INVALID_ARG, "rows or nodes is NULL");
+    if (width == 0) return fail(PG_ERR_INVALID_ARG, "width must be >= 1");
+    if (!is_pow2(n_leaves)) return fail(PG_ERR_NOT_POW2, "n_leaves=%zu is not a power of two", n_leaves);
+    if (n_leaves > dev::kNoAllocMaxLeaves)
+        return fail(PG_ERR_INVALID_ARG, "n_leaves=%zu exceeds the allocation-free limit of %llu leaves", n_leaves,
+                    (unsigned long long)dev::kNoAllocMaxLeaves);
+    if (reinterpret_cast<uintptr_t>(rows) % 8) return fail(PG_ERR_INVALID_ARG, "rows not 8-byte aligned");
+    if (reinterpret_cast<uintptr_t>(nodes) % 16) return fail(PG_ERR_INVALID_ARG, "nodes not 16-byte aligned");
+    int device = 0;
+    PG_CUDA(cudaGetDevice(&device));
+    if (device < 0 || device >= kMaxDevices) return fail(PG_ERR_INVALID_ARG, "device %d out of range", device);
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        if (scratch_ptr[device] == nullptr) {
+            pg_status s = ensure_params();
+            if (s != PG_OK) return s;
+            dev::DevConsts dc;
+            dev::make_dev_consts(g.opt, dc);
+            PG_CUDA(cudaMemcpyToSymbol(dev::c_dev, &dc, sizeof(dc)));
+            PG_CUDA(cudaDeviceGetAttribute(&sm_count[device], cudaDevAttrMultiProcessorCount, device));
+            PG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm[device], dev::k_merkle_single,
+                                                                  dev::kBlock, 0));
+            if (blocks_per_sm[device] < 1) return fail(PG_ERR_CUDA, "k_merkle_single cannot be resident");
+            void *p = nullptr;
+            PG_CUDA(cudaGetSymbolAddress(&p, dev::g_noalloc_scratch));
+            scratch_ptr[device] = static_cast<uint32_t *>(p);
+        }
+    }
+    uint32_t *scratch = scratch_ptr[device];
+    dev::TreePlan tp;
+    std::memset(&tp, 0, sizeof tp);
+    uint32_t n_counters = 0;
+    const uint32_t tasks = plan_tree(tp, rows, n_leaves, width, nodes, 0, 0, n_counters);
+    if (1 + (size_t)n_counters > dev::kNoAllocWords)
+        return fail(PG_ERR_INVALID_ARG, "n_leaves=%zu needs more scratch than the allocation-free limit", n_leaves);
+    cudaStream_t st = as_stream(stream);
+    // the array keeps the previous call's counts: clear what this call uses
+    PG_CUDA(cudaMemsetAsync(scratch, 0, sizeof(uint32_t) * (1 + (size_t)n_counters), st));
+    const uint32_t warps_per_block = dev::kBlock / 32;
+    const uint32_t want = (tasks + warps_per_block - 1) / warps_per_block;
+    const uint32_t cap = (uint32_t)(sm_count[device] * blocks_per_sm[device]);
+    const unsigned grid = want < cap ? want : cap;
+    dev::k_merkle_single<<<grid, dev::kBlock, 0, st>>>(tp, tasks, scratch + 1, scratch);
+    PG_CUDA(cudaGetLastError());
     return PG_OK;
 }
 
