@@ -49,6 +49,30 @@ typedef enum {
     PG_ERR_NOT_INIT = 7     /* pg_init() has not succeeded on this process    */
 } pg_status;
 
+/* One tree of a batch (Sec. 4.2 workload, any size/width mix). */
+typedef struct {
+    const uint64_t *rows; /* dev, n_leaves*width words, row-major            */
+    uint64_t n_leaves;    /* power of two >= 1                                */
+    uint64_t width;       /* elements per row, >= 1                           */
+    uint64_t *nodes;      /* dev, (2*n_leaves-1)*4 words, level-major output  */
+} pg_tree;
+
+/* Launch schedule of the persistent Merkle kernel.  Zero fields take the
+ * defaults.  One thread owns one state, a warp hashes 32 nodes of one level
+ * per task, and no levels are fused per block (upper levels are separate
+ * warp tasks), so the tunables are the block size, how many blocks of the
+ * persistent grid sit on each SM, and the order in which trees hand out
+ * their leaf tasks. */
+typedef struct {
+    uint32_t block;         /* threads per block: 128 or 256 (default 256)        */
+    uint32_t blocks_per_sm; /* persistent blocks per SM, capped by occupancy      */
+    uint32_t order;         /* 0 = trees as given, 1 = most work first (default 0) */
+    uint32_t reserved;      /* must be 0                                           */
+} pg_schedule;
+
+/* Opaque handle of a captured batch (see pg_batch_graph_create). */
+typedef struct pg_batch_graph pg_batch_graph;
+
 /* Library version, e.g. "pg12 1.0 sm_103a". */
 const char *pg_version(void);
 
@@ -132,6 +156,47 @@ pg_status pg_hash_rows(const uint64_t *rows, size_t n_rows, size_t width, uint64
  */
 pg_status pg_merkle_build(const uint64_t *rows, size_t n_leaves, size_t width, uint64_t *nodes,
                           uint64_t *root_out, void *stream);
+
+/*
+ * pg_merkle_build_batch -- Sec. 4.2 trees of mixed sizes and widths built
+ * in ONE persistent launch: leaf tasks of all trees come from one counter
+ * and each tree's upper levels are built by the warp that completes the
+ * second child task, so small trees' top levels overlap with other trees'
+ * leaf work.  Results are identical to pg_merkle_build on each tree alone.
+ *   trees    host array of n_trees descriptors (device buffers, caller-owned;
+ *            node buffers of different trees must not overlap).
+ *   n_trees  >= 1.
+ *   sched    NULL = defaults.
+ * Uses the pg_init workspace (plans + counters); a batch too large for it
+ * returns PG_ERR_OOM (use pg_batch_graph_create, which sizes its own).
+ */
+pg_status pg_merkle_build_batch(const pg_tree *trees, size_t n_trees, const pg_schedule *sched, void *stream);
+
+/*
+ * pg_batch_graph_create -- capture a batch into a CUDA graph: the plans are
+ * uploaded once into device memory owned by the handle, and the graph holds
+ * the counter reset and the persistent kernel.  Synchronous.  The handle
+ * reads the trees' row buffers and writes their node buffers at every
+ * launch; they must stay valid until pg_batch_graph_destroy.
+ */
+pg_status pg_batch_graph_create(const pg_tree *trees, size_t n_trees, const pg_schedule *sched,
+                                pg_batch_graph **out);
+
+/* Replay a captured batch on `stream` (asynchronous). */
+pg_status pg_batch_graph_launch(pg_batch_graph *graph, void *stream);
+
+/* Release a captured batch (synchronises with its last launch). */
+pg_status pg_batch_graph_destroy(pg_batch_graph *graph);
+
+/*
+ * pg_batch_autotune -- time each candidate schedule (block 128/256 x
+ * persistent blocks per SM x tree order) on the real batch with CUDA events
+ * and return the fastest in *best (and its time in *best_ms if non-NULL).
+ * Runs the batch several times on `stream` (outputs are overwritten with the
+ * same values); synchronous.
+ */
+pg_status pg_batch_autotune(const pg_tree *trees, size_t n_trees, void *stream, pg_schedule *best,
+                            float *best_ms);
 
 /*
  * pg_merkle_build_noalloc -- the same tree as pg_merkle_build (identical

@@ -15,6 +15,7 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -139,31 +140,43 @@ __global__ void __launch_bounds__(kSmallBlock) k_hash_rows(const uint64_t *__res
 
 // One warp task: lane i of task u at level l hashes node 32u+i of that level
 // -- a row through the sponge at level 0, else the pair of children at
-// level l-1 -- in the lane's shared-memory state slot.
+// level l-1 -- in the lane's shared-memory state slot (stride S = threads
+// per block).  Both cases feed one permutation call site, so the kernel holds
+// a single copy of the permutation code.
+template <int S>
 __device__ __forceinline__ void run_warp_task(const TreePlan &tp, uint32_t level, uint64_t u, int lane,
                                               uint64_t *slot) {
     const uint64_t n = tp.n_leaves;
     const uint64_t count = n >> level;
     const uint64_t i = u * kWarpNodes + lane;
     if (i >= count) return;
-    if (level == 0) {
-        sponge_slot<kBlock>(tp.rows + i * tp.width, tp.width, tp.vec16 != 0, slot);
-    } else {
-        const uint64_t *kids = tp.nodes + kDigest * (level_off(n, level - 1) + 2 * i);
+    const uint64_t w = tp.width;
+    const bool leaf = level == 0;
+    const uint64_t nperm = leaf ? (w == 0 ? 1 : (w + kRate - 1) / kRate) : 1;
+    const uint64_t *row = tp.rows + i * w;
+    const uint64_t *kids = tp.nodes + kDigest * (level_off(n, leaf ? 0 : level - 1) + 2 * i);
 #pragma unroll
-        for (int k = 0; k < 2 * kDigest; k += 2) {
-            uint64_t a, b;
-            ld2_cg(kids + k, a, b);
-            slot[k * kBlock] = a;
-            slot[(k + 1) * kBlock] = b;
+    for (int k = kRate; k < kT; ++k) slot[k * S] = 0;
+    for (uint64_t c = 0; c < nperm; ++c) {
+        if (leaf) {
+            uint64_t ch[kRate];
+            load_chunk(row, w, c, tp.vec16 != 0, ch);
+#pragma unroll
+            for (int k = 0; k < kRate; ++k) slot[k * S] = ch[k];
+        } else {
+#pragma unroll
+            for (int k = 0; k < 2 * kDigest; k += 2) {
+                uint64_t a, b;
+                ld2_cg(kids + k, a, b);
+                slot[k * S] = a;
+                slot[(k + 1) * S] = b;
+            }
         }
-#pragma unroll
-        for (int k = 2 * kDigest; k < kT; ++k) slot[k * kBlock] = 0;
-        permute_slot<kBlock>(slot);
+        permute_slot<S>(slot);
     }
     uint64_t *dst = tp.nodes + kDigest * (level_off(n, level) + i);
-    st2(dst, canon(slot[0]), canon(slot[kBlock]));
-    st2(dst + 2, canon(slot[2 * kBlock]), canon(slot[3 * kBlock]));
+    st2(dst, canon(slot[0]), canon(slot[S]));
+    st2(dst + 2, canon(slot[2 * S]), canon(slot[3 * S]));
 }
 
 // Persistent Merkle kernel: every warp pulls leaf tasks from a global
@@ -173,10 +186,11 @@ __device__ __forceinline__ void run_warp_task(const TreePlan &tp, uint32_t level
 // the parent and keeps climbing; the first arriver goes back for a new leaf
 // task.  Levels with at most 32 nodes have a single task and are climbed
 // without counters.  No block-wide barrier and no waiting anywhere.
-__global__ void __launch_bounds__(kBlock) k_merkle(const TreePlan *__restrict__ plans, uint32_t n_trees,
-                                                   uint32_t total_tasks, uint32_t *__restrict__ counters,
-                                                   uint32_t *__restrict__ next_task) {
-    __shared__ uint64_t slots[kT * kBlock];
+template <int S>
+__global__ void __launch_bounds__(S) k_merkle(const TreePlan *__restrict__ plans, uint32_t n_trees,
+                                             uint32_t total_tasks, uint32_t *__restrict__ counters,
+                                             uint32_t *__restrict__ next_task) {
+    __shared__ uint64_t slots[kT * S];
     uint64_t *slot = slots + threadIdx.x;
     const int lane = threadIdx.x & 31;
     const unsigned full = 0xFFFFFFFFu;
@@ -195,7 +209,7 @@ __global__ void __launch_bounds__(kBlock) k_merkle(const TreePlan *__restrict__ 
         const uint64_t n = tp.n_leaves;
         const uint32_t log_n = tp.log_n;
         uint64_t u = task - tp.leaf_task_begin;
-        run_warp_task(tp, 0, u, lane, slot);
+        run_warp_task<S>(tp, 0, u, lane, slot);
         for (uint32_t level = 1; level <= log_n; ++level) {
             const uint64_t below = n >> (level - 1);
             if (below > (uint64_t)kWarpNodes) {
@@ -211,7 +225,7 @@ __global__ void __launch_bounds__(kBlock) k_merkle(const TreePlan *__restrict__ 
                 __syncwarp();
             }
             u >>= 1;
-            run_warp_task(tp, level, u, lane, slot);
+            run_warp_task<S>(tp, level, u, lane, slot);
         }
     }
 }
@@ -241,7 +255,7 @@ __global__ void __launch_bounds__(kBlock) k_merkle_single(const TreePlan tp, uin
         task = __shfl_sync(full, task, 0);
         if (task >= total_tasks) return;
         uint64_t u = task;
-        run_warp_task(tp, 0, u, lane, slot);
+        run_warp_task<kBlock>(tp, 0, u, lane, slot);
         for (uint32_t level = 1; level <= tp.log_n; ++level) {
             if ((n >> (level - 1)) > (uint64_t)kWarpNodes) {
                 __threadfence();
@@ -255,7 +269,7 @@ __global__ void __launch_bounds__(kBlock) k_merkle_single(const TreePlan tp, uin
                 __syncwarp();
             }
             u >>= 1;
-            run_warp_task(tp, level, u, lane, slot);
+            run_warp_task<kBlock>(tp, level, u, lane, slot);
         }
     }
 }
@@ -272,7 +286,8 @@ struct Context {
     bool init = false;
     int device = -1;
     int sms = 0;
-    int merkle_blocks_per_sm = 0;
+    int merkle_blocks_per_sm = 0;      // k_merkle<256>
+    int merkle128_blocks_per_sm = 0;   // k_merkle<128>
     int permute_blocks_per_sm = 0;
     uint8_t *ws = nullptr;  // device workspace
     size_t ws_bytes = 0;
@@ -295,7 +310,7 @@ pg_status fail(pg_status s, const char *fmt, ...) {
         if (e_ != cudaSuccess) return fail(PG_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
     } while (0)
 
-constexpr size_t kWorkspaceBytes = 16u << 20;  // counters + tree plans
+constexpr size_t kWorkspaceBytes = 32u << 20;  // tree plans + arrival counters
 constexpr size_t kPlanBytes = 4u << 20;        // first part: plans; rest: counters
 
 pg_status ensure_params() {
@@ -345,8 +360,86 @@ pg_status require_init() {
     return PG_OK;
 }
 
+// Validate a batch and build its plans (in launch order).  Returns the
+// number of leaf tasks and counters through the out-parameters.
+pg_status plan_batch(const pg_tree *trees, size_t n_trees, const pg_schedule *sched,
+                     std::vector<dev::TreePlan> &plans, uint32_t &tasks, uint64_t &counters) {
+    if (!trees || n_trees == 0) return fail(PG_ERR_INVALID_ARG, "empty batch");
+    if (sched && (sched->reserved != 0 || (sched->block != 0 && sched->block != 128 && sched->block != 256) ||
+                  sched->order > 1))
+        return fail(PG_ERR_INVALID_ARG, "bad schedule");
+    std::vector<size_t> idx(n_trees);
+    for (size_t k = 0; k < n_trees; ++k) {
+        const pg_tree &t = trees[k];
+        if (!t.rows || !t.nodes) return fail(PG_ERR_INVALID_ARG, "tree %zu: rows or nodes is NULL", k);
+        if (t.width == 0) return fail(PG_ERR_INVALID_ARG, "tree %zu: width must be >= 1", k);
+        if (!is_pow2(t.n_leaves)) return fail(PG_ERR_NOT_POW2, "tree %zu: n_leaves=%llu is not a power of two", k,
+                                              (unsigned long long)t.n_leaves);
+        if (t.n_leaves > (1ull << 34)) return fail(PG_ERR_INVALID_ARG, "tree %zu: too many leaves", k);
+        if (reinterpret_cast<uintptr_t>(t.rows) % 8) return fail(PG_ERR_INVALID_ARG, "tree %zu: rows not 8-byte aligned", k);
+        if (reinterpret_cast<uintptr_t>(t.nodes) % 16)
+            return fail(PG_ERR_INVALID_ARG, "tree %zu: nodes not 16-byte aligned", k);
+        idx[k] = k;
+    }
+    if (sched && sched->order == 1) {
+        auto work = [&](size_t k) {
+            const pg_tree &t = trees[k];
+            return (double)t.n_leaves * (double)((t.width + kRate - 1) / kRate + 1);
+        };
+        std::stable_sort(idx.begin(), idx.end(), [&](size_t a, size_t b) { return work(a) > work(b); });
+    }
+    plans.assign(n_trees, dev::TreePlan{});
+    uint64_t task_sum = 0, counter_sum = 0;
+    for (size_t k = 0; k < n_trees; ++k) {
+        const pg_tree &t = trees[idx[k]];
+        uint32_t nc = 0;
+        std::memset(&plans[k], 0, sizeof(dev::TreePlan));
+        const uint32_t tk = plan_tree(plans[k], t.rows, t.n_leaves, t.width, t.nodes, (uint32_t)task_sum,
+                                      (uint32_t)counter_sum, nc);
+        task_sum += tk;
+        counter_sum += nc;
+        if (task_sum >= (1ull << 32) || counter_sum >= (1ull << 32))
+            return fail(PG_ERR_INVALID_ARG, "batch too large (task or counter index above 2^32)");
+    }
+    tasks = (uint32_t)task_sum;
+    counters = counter_sum;
+    return PG_OK;
+}
+
+// Launch the persistent Merkle kernel for `tasks` leaf tasks.
+pg_status launch_merkle(const pg_schedule *sched, const dev::TreePlan *d_plans, uint32_t n_trees, uint32_t tasks,
+                        uint32_t *d_counters, cudaStream_t st) {
+    const uint32_t block = (sched && sched->block == 128) ? 128u : 256u;
+    const int occ = block == 128 ? g.merkle128_blocks_per_sm : g.merkle_blocks_per_sm;
+    int bps = occ;
+    if (sched && sched->blocks_per_sm > 0 && (int)sched->blocks_per_sm < occ) bps = (int)sched->blocks_per_sm;
+    const uint32_t warps_per_block = block / 32;
+    const uint32_t want = (tasks + warps_per_block - 1) / warps_per_block;
+    const uint32_t cap = (uint32_t)(g.sms * bps);
+    const unsigned grid = want < cap ? want : cap;
+    if (grid == 0) return PG_OK;
+    if (block == 128)
+        dev::k_merkle<128><<<grid, 128, 0, st>>>(d_plans, n_trees, tasks, d_counters + 1, d_counters);
+    else
+        dev::k_merkle<256><<<grid, 256, 0, st>>>(d_plans, n_trees, tasks, d_counters + 1, d_counters);
+    PG_CUDA(cudaGetLastError());
+    return PG_OK;
+}
+
 }  // namespace
 }  // namespace pg12
+
+struct pg_batch_graph {
+    int device;
+    pg_schedule sched;
+    void *dmem;
+    size_t plan_bytes;
+    uint32_t n_trees, tasks;
+    uint64_t counters;
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+    cudaStream_t capture;
+};
 
 using namespace pg12;
 
@@ -396,9 +489,10 @@ pg_status pg_init(int device, const char *params_path) {
         PG_CUDA(cudaMemcpyToSymbol(dev::c_dev, &dc, sizeof(dc)));
     }
     PG_CUDA(cudaDeviceGetAttribute(&g.sms, cudaDevAttrMultiProcessorCount, device));
-    PG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g.merkle_blocks_per_sm, dev::k_merkle, dev::kBlock, 0));
+    PG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g.merkle_blocks_per_sm, dev::k_merkle<256>, 256, 0));
+    PG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g.merkle128_blocks_per_sm, dev::k_merkle<128>, 128, 0));
     PG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g.permute_blocks_per_sm, dev::k_permute, dev::kSmallBlock, 0));
-    if (g.merkle_blocks_per_sm < 1 || g.permute_blocks_per_sm < 1)
+    if (g.merkle_blocks_per_sm < 1 || g.merkle128_blocks_per_sm < 1 || g.permute_blocks_per_sm < 1)
         return fail(PG_ERR_CUDA, "kernels cannot be resident (occupancy 0)");
     void *ws = nullptr;
     cudaError_t e = cudaMalloc(&ws, kWorkspaceBytes);
@@ -475,16 +569,154 @@ pg_status pg_merkle_build(const uint64_t *rows, size_t n_leaves, size_t width, u
     auto *d_counters = reinterpret_cast<uint32_t *>(g.ws + kPlanBytes);
     PG_CUDA(cudaMemcpyAsync(d_plan, &tp, sizeof tp, cudaMemcpyHostToDevice, st));
     PG_CUDA(cudaMemsetAsync(d_counters, 0, counter_bytes, st));
-    const uint32_t warps_per_block = dev::kBlock / 32;
-    const uint32_t want = (tasks + warps_per_block - 1) / warps_per_block;
-    const uint32_t cap = (uint32_t)(g.sms * g.merkle_blocks_per_sm);
-    const unsigned grid = want < cap ? want : cap;
-    dev::k_merkle<<<grid, dev::kBlock, 0, st>>>(d_plan, 1u, tasks, d_counters + 1, d_counters);
-    PG_CUDA(cudaGetLastError());
+    s = launch_merkle(nullptr, d_plan, 1u, tasks, d_counters, st);
+    if (s != PG_OK) return s;
     if (root_out) {
         PG_CUDA(cudaMemcpyAsync(root_out, nodes + 4 * (2 * n_leaves - 2), 32, cudaMemcpyDeviceToHost, st));
         PG_CUDA(cudaStreamSynchronize(st));
     }
+    return PG_OK;
+}
+
+pg_status pg_merkle_build_batch(const pg_tree *trees, size_t n_trees, const pg_schedule *sched, void *stream) {
+    pg_status s = require_init();
+    if (s != PG_OK) return s;
+    std::vector<dev::TreePlan> plans;
+    uint32_t tasks = 0;
+    uint64_t counters = 0;
+    s = plan_batch(trees, n_trees, sched, plans, tasks, counters);
+    if (s != PG_OK) return s;
+    const size_t plan_bytes = plans.size() * sizeof(dev::TreePlan);
+    const size_t counter_bytes = sizeof(uint32_t) * (1 + (size_t)counters);
+    if (plan_bytes > kPlanBytes || counter_bytes > g.ws_bytes - kPlanBytes)
+        return fail(PG_ERR_OOM, "batch needs %zu plan bytes and %zu counter bytes; workspace holds %zu and %zu", plan_bytes,
+                    counter_bytes, kPlanBytes, g.ws_bytes - kPlanBytes);
+    cudaStream_t st = as_stream(stream);
+    auto *d_plan = reinterpret_cast<dev::TreePlan *>(g.ws);
+    auto *d_counters = reinterpret_cast<uint32_t *>(g.ws + kPlanBytes);
+    PG_CUDA(cudaMemcpyAsync(d_plan, plans.data(), plan_bytes, cudaMemcpyHostToDevice, st));
+    PG_CUDA(cudaMemsetAsync(d_counters, 0, counter_bytes, st));
+    return launch_merkle(sched, d_plan, (uint32_t)plans.size(), tasks, d_counters, st);
+}
+
+pg_status pg_batch_graph_create(const pg_tree *trees, size_t n_trees, const pg_schedule *sched,
+                                pg_batch_graph **out) {
+    pg_status s = require_init();
+    if (s != PG_OK) return s;
+    if (!out) return fail(PG_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    std::vector<dev::TreePlan> plans;
+    uint32_t tasks = 0;
+    uint64_t counters = 0;
+    s = plan_batch(trees, n_trees, sched, plans, tasks, counters);
+    if (s != PG_OK) return s;
+    auto *h = new (std::nothrow) pg_batch_graph();
+    if (!h) return fail(PG_ERR_OOM, "host allocation failed");
+    h->device = g.device;
+    std::memset(&h->sched, 0, sizeof h->sched);
+    if (sched) h->sched = *sched;
+    h->plan_bytes = plans.size() * sizeof(dev::TreePlan);
+    h->n_trees = (uint32_t)plans.size();
+    h->tasks = tasks;
+    h->counters = counters;
+    const size_t plan_bytes_aligned = (h->plan_bytes + 255) & ~(size_t)255;
+    const size_t total = plan_bytes_aligned + sizeof(uint32_t) * (1 + (size_t)counters);
+    cudaError_t e = cudaMalloc(&h->dmem, total);
+    if (e != cudaSuccess) {
+        delete h;
+        return fail(PG_ERR_OOM, "batch graph cudaMalloc(%zu): %s", total, cudaGetErrorString(e));
+    }
+    auto cleanup = [&](pg_status st_) {
+        if (h->exec) cudaGraphExecDestroy(h->exec);
+        if (h->graph) cudaGraphDestroy(h->graph);
+        if (h->capture) cudaStreamDestroy(h->capture);
+        cudaFree(h->dmem);
+        delete h;
+        return st_;
+    };
+    auto *d_plan = static_cast<dev::TreePlan *>(h->dmem);
+    auto *d_counters = reinterpret_cast<uint32_t *>(static_cast<uint8_t *>(h->dmem) + plan_bytes_aligned);
+    e = cudaMemcpy(d_plan, plans.data(), h->plan_bytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cleanup(fail(PG_ERR_CUDA, "plan upload: %s", cudaGetErrorString(e)));
+    e = cudaStreamCreateWithFlags(&h->capture, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cleanup(fail(PG_ERR_CUDA, "stream create: %s", cudaGetErrorString(e)));
+    e = cudaStreamBeginCapture(h->capture, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cleanup(fail(PG_ERR_CUDA, "begin capture: %s", cudaGetErrorString(e)));
+    cudaError_t e_memset = cudaMemsetAsync(d_counters, 0, sizeof(uint32_t) * (1 + (size_t)counters), h->capture);
+    pg_status sl = launch_merkle(&h->sched, d_plan, h->n_trees, tasks, d_counters, h->capture);
+    e = cudaStreamEndCapture(h->capture, &h->graph);
+    if (e_memset != cudaSuccess || sl != PG_OK || e != cudaSuccess)
+        return cleanup(sl != PG_OK ? sl : fail(PG_ERR_CUDA, "capture: %s", cudaGetErrorString(e != cudaSuccess ? e : e_memset)));
+    e = cudaGraphInstantiate(&h->exec, h->graph, 0);
+    if (e != cudaSuccess) return cleanup(fail(PG_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e)));
+    *out = h;
+    return PG_OK;
+}
+
+pg_status pg_batch_graph_launch(pg_batch_graph *graph, void *stream) {
+    if (!graph) return fail(PG_ERR_INVALID_ARG, "graph is NULL");
+    PG_CUDA(cudaGraphLaunch(graph->exec, as_stream(stream)));
+    return PG_OK;
+}
+
+pg_status pg_batch_graph_destroy(pg_batch_graph *graph) {
+    if (!graph) return PG_OK;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (graph->exec) cudaGraphExecDestroy(graph->exec);
+    if (graph->graph) cudaGraphDestroy(graph->graph);
+    if (graph->capture) cudaStreamDestroy(graph->capture);
+    cudaFree(graph->dmem);
+    delete graph;
+    if (e != cudaSuccess) return fail(PG_ERR_CUDA, "destroy: %s", cudaGetErrorString(e));
+    return PG_OK;
+}
+
+pg_status pg_batch_autotune(const pg_tree *trees, size_t n_trees, void *stream, pg_schedule *best,
+                            float *best_ms) {
+    pg_status s = require_init();
+    if (s != PG_OK) return s;
+    if (!best) return fail(PG_ERR_INVALID_ARG, "best is NULL");
+    cudaStream_t st = as_stream(stream);
+    cudaEvent_t e0, e1;
+    PG_CUDA(cudaEventCreate(&e0));
+    PG_CUDA(cudaEventCreate(&e1));
+    float top = -1.f;
+    pg_schedule win{};
+    const uint32_t blocks[2] = {256, 128};
+    for (uint32_t b : blocks) {
+        const int occ = b == 128 ? g.merkle128_blocks_per_sm : g.merkle_blocks_per_sm;
+        for (int bps = occ; bps >= 1 && bps >= occ - 1; --bps) {
+            for (uint32_t order = 0; order <= 1; ++order) {
+                pg_schedule c{b, (uint32_t)bps, order, 0};
+                s = pg_merkle_build_batch(trees, n_trees, &c, stream);  // warm-up
+                if (s != PG_OK) break;
+                float tot = 0.f;
+                const int reps = 3;
+                for (int r = 0; r < reps && s == PG_OK; ++r) {
+                    cudaEventRecord(e0, st);
+                    s = pg_merkle_build_batch(trees, n_trees, &c, stream);
+                    cudaEventRecord(e1, st);
+                    cudaEventSynchronize(e1);
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    tot += ms;
+                }
+                if (s != PG_OK) break;
+                const float avg = tot / reps;
+                if (top < 0.f || avg < top) {
+                    top = avg;
+                    win = c;
+                }
+            }
+            if (s != PG_OK) break;
+        }
+        if (s != PG_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s != PG_OK) return s;
+    *best = win;
+    if (best_ms) *best_ms = top;
     return PG_OK;
 }
 
