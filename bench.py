@@ -47,6 +47,14 @@ def parse_args():
     ap.add_argument("--width", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--workload", choices=["merkle", "permute", "batch", "serve"], default="merkle",
+                    help="merkle (default): one 2^log_n-leaf tree per step; permute: 2^24 raw "
+                         "permutations; batch: 64 mixed trees, one graph launch vs one launch per "
+                         "tree; serve: Poisson stream of tree-build requests")
+    ap.add_argument("--trees", type=int, default=64)
+    ap.add_argument("--requests", type=int, default=2000)
+    ap.add_argument("--rate", type=float, default=200.0)
+    ap.add_argument("--max-log-n", type=int, default=22)
     return ap.parse_args()
 
 
@@ -307,10 +315,213 @@ def run_ours(args):
     return 0
 
 
+# ------------------------------------------------------------ other workloads
+def _device_setup():
+    import torch
+    import paper_2506_09505_gb300 as pg
+    torch.cuda.set_device(0)
+    pg.load(build_if_missing=True)
+    pg.init(0)
+    return torch, pg
+
+
+def _peak_results_per_s():
+    import torch
+    peaks = measured_peaks()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    return IMAD_RESULTS_PER_CLK_SM * sms * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+
+
+def run_permute(args):
+    """2^24 independent states permuted in place (raw permutation throughput)."""
+    torch, pg = _device_setup()
+    import pg_synth
+    n = 1 << 24
+    st = pg_synth.matrix_torch(pg_synth.config_seed(2), n, 12, device="cuda")
+    for _ in range(args.warmup):
+        pg.permute_batch(st)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        pg.permute_batch(st)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    rate = n / (ms / 1e3)
+    ach = rate * MUL_RESULTS_PER_PERM
+    print(json.dumps({"workload": "permute 2^24 states in place", "metric": "perms/s", "value": rate,
+                      "ms_per_step": ms, "steps": args.steps, "kernel": "k_permute",
+                      "roofline": {"bound": "alu", "achieved": ach / 1e12, "peak": _peak_results_per_s() / 1e12,
+                                   "unit": "T mul32-results/s", "frac": ach / _peak_results_per_s()}}), flush=True)
+    return 0
+
+
+def _batch_sizes(seed, trees, max_log_n):
+    import pg_synth
+    u = pg_synth.uniform01(seed, trees)
+    ks = [12 + int(v * (min(max_log_n, 20) - 12 + 1)) for v in u]
+    widths = [(8, 16, 32, 64, 128)[int(v)] for v in pg_synth.integers(seed + 1, trees, 0, 4)]
+    return [(min(k, 20), w) for k, w in zip(ks, widths)]
+
+
+def run_batch(args):
+    """64 trees of mixed sizes and widths: one captured persistent launch (autotuned
+    schedule) against one pg_merkle_build launch per tree, same GPU, same inputs."""
+    torch, pg = _device_setup()
+    import pg_synth
+    sizes = _batch_sizes(pg_synth.config_seed(4), args.trees, args.max_log_n)
+    rows = [pg_synth.matrix_torch(pg_synth.tree_seed(pg_synth.config_seed(4), k), 1 << lg, w, device="cuda")
+            for k, (lg, w) in enumerate(sizes)]
+    perms = sum((1 << lg) * ((w + 7) // 8) + (1 << lg) - 1 for lg, w in sizes)
+    nodes = pg.alloc_nodes(rows)
+    best, tune_ms = pg.batch_autotune(rows, nodes)
+    g = pg.BatchGraph(rows, nodes, schedule=best)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(args.warmup):
+        g.launch()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(args.steps):
+        g.launch()
+    e1.record()
+    torch.cuda.synchronize()
+    ms_batch = e0.elapsed_time(e1) / args.steps
+    batch_out = [t.clone() for t in nodes]
+    single = [torch.empty_like(t) for t in nodes]
+    for _ in range(args.warmup):
+        for r, nd in zip(rows, single):
+            pg.merkle_build(r, nd)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(args.steps):
+        for r, nd in zip(rows, single):
+            pg.merkle_build(r, nd)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_single = e0.elapsed_time(e1) / args.steps
+    same = all(torch.equal(a, b) for a, b in zip(batch_out, single))
+    g.close()
+    peak = _peak_results_per_s()
+    print(json.dumps({
+        "workload": f"batch of {len(sizes)} trees, 2^k leaves k in [12,20], widths in {{8..128}}",
+        "perms_per_step": perms, "trees": [[lg, w] for lg, w in sizes],
+        "batched_graph": {"ms": ms_batch, "perms_per_s": perms / (ms_batch / 1e3),
+                          "imad_frac": perms * MUL_RESULTS_PER_PERM / (ms_batch / 1e3) / peak,
+                          "schedule": best, "autotune_best_ms": tune_ms},
+        "one_launch_per_tree": {"ms": ms_single, "perms_per_s": perms / (ms_single / 1e3),
+                                "imad_frac": perms * MUL_RESULTS_PER_PERM / (ms_single / 1e3) / peak},
+        "speedup": ms_single / ms_batch, "bit_identical": same}), flush=True)
+    return 0
+
+
+def run_serve(args):
+    """Poisson stream of tree builds through the serving runtime against a
+    sequential FIFO of single-tree builds on the same arrival trace."""
+    torch, pg = _device_setup()
+    import numpy as np
+    import pg_synth
+    seed = pg_synth.config_seed(5)
+    nreq = args.requests
+    gaps = -np.log(1.0 - pg_synth.uniform01(seed, nreq)) / args.rate
+    arrivals = np.cumsum(gaps)
+    ks = pg_synth.integers(seed + 1, nreq, 10, args.max_log_n)
+    ws = [(8, 32, 128, 256)[int(v)] for v in pg_synth.integers(seed + 2, nreq, 0, 3)]
+    perms = [int((1 << int(k)) * ((w + 7) // 8) + (1 << int(k)) - 1) for k, w in zip(ks, ws)]
+    # payloads are materialised on the device ahead of their arrival (not timed); to bound
+    # memory, requests reuse a small set of row buffers generated per (k, w) shape
+    cache = {}
+
+    def rows_for(i):
+        key = (int(ks[i]), ws[i])
+        if key not in cache:
+            cache[key] = pg_synth.matrix_torch(pg_synth.tree_seed(seed, len(cache)), 1 << key[0], key[1], device="cuda")
+        return cache[key]
+
+    for i in range(nreq):
+        rows_for(i)
+    torch.cuda.synchronize()
+    pool = int(min(torch.cuda.mem_get_info()[0] * 0.5, 64 << 30))
+    srv = pg.Server(pool_bytes=pool, max_batch=256, max_inflight=2, schedule={"order": 1})
+    import time as _t
+    lat = {}
+    pending = []
+
+    def reap():
+        keep = []
+        for rid in pending:
+            info = srv.query(rid)
+            if info["state"] in (pg.REQ_DONE, pg.REQ_FAILED):
+                if info["state"] != pg.REQ_DONE:
+                    raise RuntimeError(f"request {rid} failed")
+                lat[rid] = info["done_s"] - info["submit_s"]
+                srv.release(rid)
+            else:
+                keep.append(rid)
+        pending[:] = keep
+
+    t_start = _t.perf_counter()
+    for i in range(nreq):
+        while True:
+            now = _t.perf_counter() - t_start
+            if arrivals[i] <= now:
+                break
+            reap()
+            now = _t.perf_counter() - t_start
+            if arrivals[i] > now:
+                _t.sleep(min(arrivals[i] - now, 0.002))
+        pending.append(srv.submit(rows_for(i)))
+    while pending:
+        reap()
+        _t.sleep(0.001)
+        if _t.perf_counter() - t_start > 900:
+            raise RuntimeError("serving run did not finish")
+    t_end = _t.perf_counter() - t_start
+    srv.close()
+    lat = list(lat.values())
+    lat = np.array(lat)
+    total_perms = sum(perms)
+    # sequential FIFO: one pg_merkle_build per request in arrival order, each
+    # starting at max(arrival, previous finish); device time per build measured
+    times = {}
+    for key, r in cache.items():
+        nd = torch.empty((2 * r.shape[0] - 1, 4), dtype=torch.int64, device="cuda")
+        pg.merkle_build(r, nd)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(3):
+            pg.merkle_build(r, nd)
+        e1.record()
+        torch.cuda.synchronize()
+        times[key] = e0.elapsed_time(e1) / 3 / 1e3
+    fin, seq_lat = 0.0, []
+    for i in range(nreq):
+        start = max(arrivals[i], fin)
+        fin = start + times[(int(ks[i]), ws[i])]
+        seq_lat.append(fin - arrivals[i])
+    seq_lat = np.array(seq_lat)
+    print(json.dumps({
+        "workload": f"serve {nreq} Poisson requests at {args.rate}/s, 2^k leaves k in [10,{args.max_log_n}], widths {{8,32,128,256}}",
+        "total_perms": total_perms,
+        "server": {"makespan_s": t_end, "perms_per_s": total_perms / t_end,
+                   "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99))},
+        "sequential_fifo": {"makespan_s": float(fin), "perms_per_s": total_perms / fin,
+                            "p50_latency_s": float(np.percentile(seq_lat, 50)),
+                            "p99_latency_s": float(np.percentile(seq_lat, 99))},
+        "offered_perms_per_s": total_perms / float(arrivals[-1])}), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "permute":
+        return run_permute(args)
+    if args.workload == "batch":
+        return run_batch(args)
+    if args.workload == "serve":
+        return run_serve(args)
     return run_ours(args)
 
 

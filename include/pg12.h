@@ -73,6 +73,41 @@ typedef struct {
 /* Opaque handle of a captured batch (see pg_batch_graph_create). */
 typedef struct pg_batch_graph pg_batch_graph;
 
+/* Serving runtime (continuous batching of tree builds); see pg_server_create. */
+typedef struct pg_server pg_server;
+
+typedef struct {
+    size_t pool_bytes;     /* device memory for node buffers (admission budget); 0 = 4 GiB */
+    uint32_t max_batch;    /* requests per launch (0 = 256)                               */
+    uint32_t max_inflight; /* batches on the device at once, one stream each (0 = 2, <= 8) */
+    pg_schedule sched;     /* launch schedule of every batch (zeros = defaults)          */
+} pg_server_config;
+
+/* Request states reported by pg_server_query. */
+enum { PG_REQ_QUEUED = 0, PG_REQ_RUNNING = 1, PG_REQ_DONE = 2, PG_REQ_FAILED = 3 };
+
+typedef struct {
+    int32_t state;          /* PG_REQ_*                                                  */
+    int32_t batch_size;     /* requests in the launch that built it (0 until launched)   */
+    double submit_s;        /* host clock (s since pg_server_create) at submission        */
+    double launch_s;        /* ... when its batch was launched                           */
+    double done_s;          /* ... when the server saw its batch complete                */
+    const uint64_t *nodes;  /* dev, (2N-1)*4 words in the server's pool, once admitted   */
+} pg_request_info;
+
+/* Element-wise field operations (pg_field_eval / pg_field_bench), the GPU
+ * counterparts of Table 1's basic functions. */
+enum {
+    PG_OP_ADD = 1,       /* a + b                          (Alg. 4, add)            */
+    PG_OP_SUB = 2,       /* a - b                          (Alg. 6, sub)            */
+    PG_OP_MUL = 3,       /* a * b                          (mult_128)               */
+    PG_OP_SQR = 4,       /* a * a                          (square_128)             */
+    PG_OP_REDUCE = 5,    /* (b * 2^64 + a) mod p           (Alg. 2, reduce_128_64)  */
+    PG_OP_MUL_SMALL = 6, /* a * (b mod 2^8)                (mult_72)                */
+    PG_OP_SBOX = 7,      /* a^7                            (Alg. 1 SBox)            */
+    PG_OP_DOT12 = 8      /* 12-term dot product, bench only (spmv/mmult rows)       */
+};
+
 /* Library version, e.g. "pg12 1.0 sm_103a". */
 const char *pg_version(void);
 
@@ -197,6 +232,49 @@ pg_status pg_batch_graph_destroy(pg_batch_graph *graph);
  */
 pg_status pg_batch_autotune(const pg_tree *trees, size_t n_trees, void *stream, pg_schedule *best,
                             float *best_ms);
+
+/*
+ * Serving runtime: a host thread admits tree-build requests into node
+ * buffers carved from a device memory pool (admission by free HBM: a
+ * request waits while its (2N-1)*32-byte node buffer does not fit), and
+ * launches every admitted request that is waiting as one batch
+ * (pg_merkle_build_batch's kernel) on one of max_inflight streams, so
+ * requests that arrive while earlier batches run join the next launch and
+ * their work overlaps on the device.  Results equal pg_merkle_build on each
+ * tree alone.  Row buffers stay caller-owned and must remain valid until the
+ * request is done.  All calls are thread-safe.
+ *   pg_server_create   needs pg_init(); allocates the pool and per-stream
+ *                      plan/counter buffers.
+ *   pg_server_submit   queue a build (rows dev, n_leaves pow2, width >= 1);
+ *                      a request larger than the whole pool fails with
+ *                      PG_ERR_OOM.  Returns its id.
+ *   pg_server_query    state, timestamps and node pointer of a request.
+ *   pg_server_release  give a finished request's node buffer back to the pool.
+ *   pg_server_drain    wait (bounded by timeout_s, else PG_ERR_TIMEOUT) until
+ *                      every submitted request is done or failed.
+ *   pg_server_destroy  stop the thread, wait for the device, free everything.
+ */
+pg_status pg_server_create(const pg_server_config *cfg, pg_server **out);
+pg_status pg_server_submit(pg_server *srv, const uint64_t *rows, uint64_t n_leaves, uint64_t width, uint64_t *id_out);
+pg_status pg_server_query(pg_server *srv, uint64_t id, pg_request_info *info);
+pg_status pg_server_release(pg_server *srv, uint64_t id);
+pg_status pg_server_drain(pg_server *srv, double timeout_s);
+pg_status pg_server_destroy(pg_server *srv);
+
+/*
+ * pg_field_eval -- out[i] = op(a[i], b[i]) mod p, canonical, for the ops
+ * PG_OP_ADD .. PG_OP_SBOX (b may be NULL for one-operand ops; it is read as
+ * 0).  a, b, out: dev, n words each; any 64-bit input words.  Asynchronous.
+ */
+pg_status pg_field_eval(int op, const uint64_t *a, const uint64_t *b, uint64_t *out, size_t n, void *stream);
+
+/*
+ * pg_field_bench -- throughput of one operation on the current device
+ * (twelve independent chains per thread, grid = SMs x occupancy): results
+ * per second and per SM clock (clock64-timed).  Synchronous; allocates and
+ * frees two small device buffers.
+ */
+pg_status pg_field_bench(int op, double *ops_per_s, double *ops_per_clk_sm);
 
 /*
  * pg_merkle_build_noalloc -- the same tree as pg_merkle_build (identical

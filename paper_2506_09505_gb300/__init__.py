@@ -53,6 +53,20 @@ class Schedule(ctypes.Structure):
     def as_dict(self):
         return {"block": self.block, "blocks_per_sm": self.blocks_per_sm, "order": self.order}
 
+class ServerConfig(ctypes.Structure):
+    """pg_server_config of include/pg12.h."""
+    _fields_ = [("pool_bytes", ctypes.c_size_t), ("max_batch", ctypes.c_uint32),
+                ("max_inflight", ctypes.c_uint32), ("sched", Schedule)]
+
+
+class RequestInfo(ctypes.Structure):
+    """pg_request_info of include/pg12.h."""
+    _fields_ = [("state", ctypes.c_int32), ("batch_size", ctypes.c_int32), ("submit_s", ctypes.c_double),
+                ("launch_s", ctypes.c_double), ("done_s", ctypes.c_double), ("nodes", ctypes.c_void_p)]
+
+
+REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
+
 # name -> (restype, argtypes) for every symbol declared in include/pg12.h
 SIGNATURES = {
     "pg_version": (ctypes.c_char_p, []),
@@ -76,7 +90,20 @@ SIGNATURES = {
     "pg_batch_graph_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "pg_batch_autotune": (ctypes.c_int, [ctypes.POINTER(Tree), ctypes.c_size_t, ctypes.c_void_p,
                                          ctypes.POINTER(Schedule), ctypes.POINTER(ctypes.c_float)]),
+    "pg_server_create": (ctypes.c_int, [ctypes.POINTER(ServerConfig), ctypes.POINTER(ctypes.c_void_p)]),
+    "pg_server_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64,
+                                        ctypes.POINTER(ctypes.c_uint64)]),
+    "pg_server_query": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(RequestInfo)]),
+    "pg_server_release": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64]),
+    "pg_server_drain": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
+    "pg_server_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "pg_field_eval": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_size_t, ctypes.c_void_p]),
+    "pg_field_bench": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_double)]),
 }
+
+OPS = {"add": 1, "sub": 2, "mul": 3, "sqr": 4, "reduce": 5, "mul_small": 6, "sbox": 7, "dot12": 8}
 
 
 def lib_path() -> str:
@@ -293,6 +320,85 @@ def batch_autotune(rows_list, nodes_list=None, stream=None):
     _check(load().pg_batch_autotune(arr, len(rows_list), _stream(stream), ctypes.byref(best),
                                     ctypes.byref(ms)))
     return best.as_dict(), float(ms.value)
+
+
+def field_eval(op: str, a, b=None, stream=None):
+    """Element-wise field operation on CUDA tensors (canonical result)."""
+    import torch
+    out = torch.empty_like(a)
+    _check(load().pg_field_eval(OPS[op], _dev_ptr(a, "a"), _dev_ptr(b, "b") if b is not None else None,
+                                _dev_ptr(out, "out"), a.numel(), _stream(stream)))
+    return out
+
+
+def field_bench(op: str):
+    """(results per second, results per SM clock) of one field operation."""
+    rate, per_clk = ctypes.c_double(), ctypes.c_double()
+    _check(load().pg_field_bench(OPS[op], ctypes.byref(rate), ctypes.byref(per_clk)))
+    return rate.value, per_clk.value
+
+
+class Server:
+    """Continuous-batching tree-build server (pg_server_* of include/pg12.h)."""
+
+    def __init__(self, pool_bytes=0, max_batch=0, max_inflight=0, schedule=None):
+        sc = Schedule()
+        if schedule:
+            sc.block, sc.blocks_per_sm, sc.order = (schedule.get("block", 0), schedule.get("blocks_per_sm", 0),
+                                                    schedule.get("order", 0))
+        cfg = ServerConfig(pool_bytes, max_batch, max_inflight, sc)
+        self._h = ctypes.c_void_p()
+        _check(load().pg_server_create(ctypes.byref(cfg), ctypes.byref(self._h)))
+
+    def submit(self, rows) -> int:
+        """Queue a build of the (N, w) CUDA tensor ``rows`` (kept alive by the caller)."""
+        rid = ctypes.c_uint64()
+        _check(load().pg_server_submit(self._h, _dev_ptr(rows, "rows"), rows.shape[0], rows.shape[1],
+                                       ctypes.byref(rid)))
+        return int(rid.value)
+
+    def query(self, rid: int) -> dict:
+        info = RequestInfo()
+        _check(load().pg_server_query(self._h, rid, ctypes.byref(info)))
+        return {"state": info.state, "batch_size": info.batch_size, "submit_s": info.submit_s,
+                "launch_s": info.launch_s, "done_s": info.done_s, "nodes": info.nodes}
+
+    def nodes(self, rid: int, n_leaves: int):
+        """The finished request's node buffer as a (2N-1, 4) int64 CUDA tensor.
+
+        A view of the server's pool (no copy): valid until release(rid).
+        """
+        import torch
+        info = self.query(rid)
+        if info["state"] != REQ_DONE:
+            raise RuntimeError(f"request {rid} is not done (state {info['state']})")
+        view = _DeviceView(info["nodes"], (2 * n_leaves - 1, DIGEST))
+        return torch.as_tensor(view, device="cuda")
+
+    def release(self, rid: int) -> None:
+        _check(load().pg_server_release(self._h, rid))
+
+    def drain(self, timeout_s: float = 60.0) -> None:
+        _check(load().pg_server_drain(self._h, timeout_s))
+
+    def close(self) -> None:
+        if self._h:
+            _check(load().pg_server_destroy(self._h))
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class _DeviceView:
+    """Exposes a raw device pointer to torch through __cuda_array_interface__."""
+
+    def __init__(self, ptr: int, shape):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": "<i8", "data": (int(ptr), False),
+                                         "version": 3, "strides": None}
 
 
 def level_offsets(n_leaves: int):

@@ -22,7 +22,9 @@ OBJDIR = os.path.join(HERE, "_build")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
-SOURCES = ["params.cpp", "pg12.cu"]
+# extra nvcc flags for tuning builds, e.g. PG12_NVCC_FLAGS="-DPG12_MERKLE_MIN_BLOCKS=4"
+EXTRA = os.environ.get("PG12_NVCC_FLAGS", "").split()
+SOURCES = ["params.cpp", "pg12.cu", "ops.cu"]
 
 
 def nvcc() -> str:
@@ -49,7 +51,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def compile_one(src: str) -> str:
         obj = os.path.join(OBJDIR, src + ".o")
-        cmd = [cc, *ARCH, *COMMON, "-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [cc, *ARCH, *COMMON, *EXTRA, "-c", os.path.join(CSRC, src), "-o", obj]
         if src.endswith(".cu") and verbose:
             cmd += ["-Xptxas", "-v"]
         res = subprocess.run(cmd, capture_output=True, text=True)

@@ -16,6 +16,12 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <thread>
+#include <unordered_map>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -28,6 +34,9 @@ namespace dev {
 // ------------------------------------------------------------- geometry
 constexpr int kBlock = 256;     // threads per Merkle block (8 independent warps)
 constexpr int kWarpNodes = 32;  // nodes of one level hashed by one warp task
+#ifndef PG12_MERKLE_MIN_BLOCKS
+#define PG12_MERKLE_MIN_BLOCKS 3  // resident 256-thread blocks per SM the register budget targets
+#endif
 constexpr int kMaxLevels = 40;
 
 // One tree of a build.  A "task" is 32 consecutive nodes of one level,
@@ -187,7 +196,7 @@ __device__ __forceinline__ void run_warp_task(const TreePlan &tp, uint32_t level
 // task.  Levels with at most 32 nodes have a single task and are climbed
 // without counters.  No block-wide barrier and no waiting anywhere.
 template <int S>
-__global__ void __launch_bounds__(S) k_merkle(const TreePlan *__restrict__ plans, uint32_t n_trees,
+__global__ void __launch_bounds__(S, PG12_MERKLE_MIN_BLOCKS * 256 / S) k_merkle(const TreePlan *__restrict__ plans, uint32_t n_trees,
                                              uint32_t total_tasks, uint32_t *__restrict__ counters,
                                              uint32_t *__restrict__ next_task) {
     __shared__ uint64_t slots[kT * S];
@@ -303,6 +312,18 @@ pg_status fail(pg_status s, const char *fmt, ...) {
     va_end(ap);
     return s;
 }
+
+}  // namespace
+
+int set_error(int status, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return status;
+}
+
+namespace {
 
 #define PG_CUDA(call)                                                                         \
     do {                                                                                      \
@@ -440,6 +461,212 @@ struct pg_batch_graph {
     cudaGraphExec_t exec;
     cudaStream_t capture;
 };
+
+// ------------------------------------------------------------ serving runtime
+namespace pg12 {
+namespace {
+
+// First-fit allocator over offsets of one device region (256-byte units),
+// coalescing freed neighbours.
+class PoolAlloc {
+  public:
+    void init(size_t bytes) {
+        free_.clear();
+        free_[0] = bytes;
+        total_ = bytes;
+    }
+    static size_t round(size_t b) { return (b + 255) & ~(size_t)255; }
+    bool alloc(size_t bytes, size_t &off) {
+        bytes = round(bytes);
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second < bytes) continue;
+            off = it->first;
+            const size_t rest = it->second - bytes;
+            free_.erase(it);
+            if (rest) free_[off + bytes] = rest;
+            return true;
+        }
+        return false;
+    }
+    void release(size_t off, size_t bytes) {
+        bytes = round(bytes);
+        auto it = free_.emplace(off, bytes).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+    size_t total() const { return total_; }
+
+  private:
+    std::map<size_t, size_t> free_;
+    size_t total_ = 0;
+};
+
+struct ServerReq {
+    const uint64_t *rows = nullptr;
+    uint64_t n = 0, w = 0;
+    size_t off = 0, bytes = 0;
+    bool admitted = false;
+    int state = PG_REQ_QUEUED;
+    int batch = 0;
+    double t_submit = 0, t_launch = 0, t_done = 0;
+};
+
+struct ServerSlot {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    dev::TreePlan *d_plans = nullptr;
+    dev::TreePlan *h_plans = nullptr;  // pinned staging for the plan upload
+    uint32_t *d_counters = nullptr;
+    size_t counter_words = 0;
+    std::vector<uint64_t> ids;
+    bool busy = false;
+};
+
+}  // namespace
+}  // namespace pg12
+
+struct pg_server {
+    int device = 0;
+    pg_server_config cfg{};
+    uint8_t *pool = nullptr;
+    pg12::PoolAlloc alloc;
+    std::vector<pg12::ServerSlot> slots;
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<uint64_t> queue;  // submitted, not yet launched (arrival order)
+    std::unordered_map<uint64_t, pg12::ServerReq> reqs;
+    uint64_t next_id = 1;
+    size_t outstanding = 0;  // submitted and not yet done or failed
+    bool stop = false;
+    std::thread worker;
+    std::chrono::steady_clock::time_point t0;
+    double now() const {
+        return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+};
+
+namespace pg12 {
+namespace {
+
+// One scheduling pass (called with the server lock held): retire finished
+// batches, then launch what is admissible on a free stream.  Returns true if
+// anything changed.
+bool server_step(pg_server *s) {
+    bool progress = false;
+    for (auto &sl : s->slots) {
+        if (!sl.busy) continue;
+        const cudaError_t q = cudaEventQuery(sl.done);
+        if (q == cudaErrorNotReady) continue;
+        const double t = s->now();
+        for (uint64_t id : sl.ids) {
+            auto &r = s->reqs[id];
+            r.state = q == cudaSuccess ? PG_REQ_DONE : PG_REQ_FAILED;
+            r.t_done = t;
+            --s->outstanding;
+        }
+        sl.ids.clear();
+        sl.busy = false;
+        progress = true;
+    }
+    if (s->queue.empty()) return progress;
+    ServerSlot *slot = nullptr;
+    for (auto &sl : s->slots)
+        if (!sl.busy) {
+            slot = &sl;
+            break;
+        }
+    if (!slot) return progress;
+    // admit in arrival order; a request whose node buffer does not fit waits
+    // while later, smaller ones may pass it
+    std::vector<uint64_t> take;
+    size_t words = 1;
+    for (auto it = s->queue.begin(); it != s->queue.end() && take.size() < s->cfg.max_batch;) {
+        auto &r = s->reqs[*it];
+        const size_t need = (size_t)((r.n + dev::kWarpNodes - 1) / dev::kWarpNodes) + 1;
+        if (words + need > slot->counter_words) break;
+        if (!r.admitted) {
+            size_t off = 0;
+            if (s->alloc.alloc(r.bytes, off)) {
+                r.off = off;
+                r.admitted = true;
+            }
+        }
+        if (r.admitted) {
+            take.push_back(*it);
+            words += need;
+            it = s->queue.erase(it);
+        } else {
+            ++it;
+        }
+    }
+    if (take.empty()) return progress;
+    std::vector<pg_tree> trees(take.size());
+    for (size_t k = 0; k < take.size(); ++k) {
+        const auto &r = s->reqs[take[k]];
+        trees[k].rows = r.rows;
+        trees[k].n_leaves = r.n;
+        trees[k].width = r.w;
+        trees[k].nodes = reinterpret_cast<uint64_t *>(s->pool + r.off);
+    }
+    std::vector<dev::TreePlan> plans;
+    uint32_t tasks = 0;
+    uint64_t counters = 0;
+    pg_status st = plan_batch(trees.data(), trees.size(), &s->cfg.sched, plans, tasks, counters);
+    cudaError_t e = cudaSuccess;
+    if (st == PG_OK) {
+        std::memcpy(slot->h_plans, plans.data(), plans.size() * sizeof(dev::TreePlan));
+        e = cudaMemcpyAsync(slot->d_plans, slot->h_plans, plans.size() * sizeof(dev::TreePlan),
+                            cudaMemcpyHostToDevice, slot->stream);
+        if (e == cudaSuccess)
+            e = cudaMemsetAsync(slot->d_counters, 0, sizeof(uint32_t) * (1 + (size_t)counters), slot->stream);
+        if (e == cudaSuccess)
+            st = launch_merkle(&s->cfg.sched, slot->d_plans, (uint32_t)plans.size(), tasks, slot->d_counters,
+                               slot->stream);
+        if (e == cudaSuccess && st == PG_OK) e = cudaEventRecord(slot->done, slot->stream);
+    }
+    const double t = s->now();
+    if (st != PG_OK || e != cudaSuccess) {
+        for (uint64_t id : take) {
+            auto &r = s->reqs[id];
+            r.state = PG_REQ_FAILED;
+            r.t_done = t;
+            --s->outstanding;
+        }
+        return true;
+    }
+    for (uint64_t id : take) {
+        auto &r = s->reqs[id];
+        r.state = PG_REQ_RUNNING;
+        r.t_launch = t;
+        r.batch = (int)take.size();
+    }
+    slot->ids = take;
+    slot->busy = true;
+    return true;
+}
+
+void server_loop(pg_server *s) {
+    cudaSetDevice(s->device);
+    std::unique_lock<std::mutex> lk(s->mu);
+    while (!s->stop) {
+        const bool progress = server_step(s);
+        if (progress) s->cv.notify_all();
+        else s->cv.wait_for(lk, std::chrono::microseconds(50));
+    }
+}
+
+}  // namespace
+}  // namespace pg12
 
 using namespace pg12;
 
@@ -717,6 +944,142 @@ pg_status pg_batch_autotune(const pg_tree *trees, size_t n_trees, void *stream, 
     if (s != PG_OK) return s;
     *best = win;
     if (best_ms) *best_ms = top;
+    return PG_OK;
+}
+
+pg_status pg_server_create(const pg_server_config *cfg, pg_server **out) {
+    pg_status s = require_init();
+    if (s != PG_OK) return s;
+    if (!out) return fail(PG_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    auto *srv = new (std::nothrow) pg_server();
+    if (!srv) return fail(PG_ERR_OOM, "host allocation failed");
+    if (cfg) srv->cfg = *cfg;
+    if (srv->cfg.pool_bytes == 0) srv->cfg.pool_bytes = (size_t)4 << 30;
+    if (srv->cfg.max_batch == 0) srv->cfg.max_batch = 256;
+    if (srv->cfg.max_inflight == 0) srv->cfg.max_inflight = 2;
+    if (srv->cfg.max_inflight > 8) srv->cfg.max_inflight = 8;
+    srv->device = g.device;
+    srv->t0 = std::chrono::steady_clock::now();
+    auto cleanup = [&](pg_status st_) {
+        for (auto &sl : srv->slots) {
+            if (sl.stream) cudaStreamDestroy(sl.stream);
+            if (sl.done) cudaEventDestroy(sl.done);
+            if (sl.d_plans) cudaFree(sl.d_plans);
+            if (sl.d_counters) cudaFree(sl.d_counters);
+            if (sl.h_plans) cudaFreeHost(sl.h_plans);
+        }
+        if (srv->pool) cudaFree(srv->pool);
+        delete srv;
+        return st_;
+    };
+    cudaError_t e = cudaMalloc(&srv->pool, srv->cfg.pool_bytes);
+    if (e != cudaSuccess) return cleanup(fail(PG_ERR_OOM, "server pool cudaMalloc(%zu): %s", srv->cfg.pool_bytes, cudaGetErrorString(e)));
+    srv->alloc.init(srv->cfg.pool_bytes);
+    srv->slots.resize(srv->cfg.max_inflight);
+    for (auto &sl : srv->slots) {
+        sl.counter_words = srv->cfg.pool_bytes / 512 + 1024 + 2 * (size_t)srv->cfg.max_batch;
+        const size_t plan_bytes = sizeof(dev::TreePlan) * srv->cfg.max_batch;
+        e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaMalloc(&sl.d_plans, plan_bytes);
+        if (e == cudaSuccess) e = cudaMalloc(&sl.d_counters, sizeof(uint32_t) * sl.counter_words);
+        if (e == cudaSuccess) e = cudaMallocHost(&sl.h_plans, plan_bytes);
+        if (e != cudaSuccess) return cleanup(fail(PG_ERR_OOM, "server stream buffers: %s", cudaGetErrorString(e)));
+    }
+    srv->worker = std::thread(server_loop, srv);
+    *out = srv;
+    return PG_OK;
+}
+
+pg_status pg_server_submit(pg_server *srv, const uint64_t *rows, uint64_t n_leaves, uint64_t width, uint64_t *id_out) {
+    if (!srv || !rows || !id_out) return fail(PG_ERR_INVALID_ARG, "NULL argument");
+    if (width == 0) return fail(PG_ERR_INVALID_ARG, "width must be >= 1");
+    if (!is_pow2(n_leaves)) return fail(PG_ERR_NOT_POW2, "n_leaves=%llu is not a power of two", (unsigned long long)n_leaves);
+    if (reinterpret_cast<uintptr_t>(rows) % 8) return fail(PG_ERR_INVALID_ARG, "rows not 8-byte aligned");
+    const size_t bytes = (size_t)(2 * n_leaves - 1) * 32;
+    if (PoolAlloc::round(bytes) > srv->alloc.total())
+        return fail(PG_ERR_OOM, "request needs %zu node bytes, the pool holds %zu", bytes, srv->alloc.total());
+    if ((n_leaves + dev::kWarpNodes - 1) / dev::kWarpNodes + 2 > srv->slots[0].counter_words)
+        return fail(PG_ERR_OOM, "request needs more arrival counters than a stream holds");
+    std::lock_guard<std::mutex> lk(srv->mu);
+    const uint64_t id = srv->next_id++;
+    ServerReq r;
+    r.rows = rows;
+    r.n = n_leaves;
+    r.w = width;
+    r.bytes = bytes;
+    r.t_submit = srv->now();
+    srv->reqs.emplace(id, r);
+    srv->queue.push_back(id);
+    ++srv->outstanding;
+    *id_out = id;
+    srv->cv.notify_all();
+    return PG_OK;
+}
+
+pg_status pg_server_query(pg_server *srv, uint64_t id, pg_request_info *info) {
+    if (!srv || !info) return fail(PG_ERR_INVALID_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(srv->mu);
+    auto it = srv->reqs.find(id);
+    if (it == srv->reqs.end()) return fail(PG_ERR_INVALID_ARG, "unknown request %llu", (unsigned long long)id);
+    const auto &r = it->second;
+    info->state = r.state;
+    info->batch_size = r.batch;
+    info->submit_s = r.t_submit;
+    info->launch_s = r.t_launch;
+    info->done_s = r.t_done;
+    info->nodes = r.admitted ? reinterpret_cast<const uint64_t *>(srv->pool + r.off) : nullptr;
+    return PG_OK;
+}
+
+pg_status pg_server_release(pg_server *srv, uint64_t id) {
+    if (!srv) return fail(PG_ERR_INVALID_ARG, "NULL server");
+    std::lock_guard<std::mutex> lk(srv->mu);
+    auto it = srv->reqs.find(id);
+    if (it == srv->reqs.end()) return fail(PG_ERR_INVALID_ARG, "unknown request %llu", (unsigned long long)id);
+    if (it->second.state != PG_REQ_DONE && it->second.state != PG_REQ_FAILED)
+        return fail(PG_ERR_INVALID_ARG, "request %llu is still in flight", (unsigned long long)id);
+    if (it->second.admitted) srv->alloc.release(it->second.off, it->second.bytes);
+    srv->reqs.erase(it);
+    srv->cv.notify_all();
+    return PG_OK;
+}
+
+pg_status pg_server_drain(pg_server *srv, double timeout_s) {
+    if (!srv) return fail(PG_ERR_INVALID_ARG, "NULL server");
+    const auto deadline = std::chrono::steady_clock::now() + std::chrono::duration<double>(timeout_s);
+    std::unique_lock<std::mutex> lk(srv->mu);
+    while (srv->outstanding > 0) {
+        if (srv->cv.wait_until(lk, deadline) == std::cv_status::timeout && srv->outstanding > 0)
+            return fail(PG_ERR_TIMEOUT, "drain: %zu requests still outstanding after %.3f s", srv->outstanding, timeout_s);
+    }
+    return PG_OK;
+}
+
+pg_status pg_server_destroy(pg_server *srv) {
+    if (!srv) return PG_OK;
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        srv->stop = true;
+    }
+    srv->cv.notify_all();
+    if (srv->worker.joinable()) srv->worker.join();
+    cudaError_t e = cudaSuccess;
+    for (auto &sl : srv->slots) {
+        if (sl.stream) {
+            cudaError_t e2 = cudaStreamSynchronize(sl.stream);
+            if (e == cudaSuccess) e = e2;
+            cudaStreamDestroy(sl.stream);
+        }
+        if (sl.done) cudaEventDestroy(sl.done);
+        if (sl.d_plans) cudaFree(sl.d_plans);
+        if (sl.d_counters) cudaFree(sl.d_counters);
+        if (sl.h_plans) cudaFreeHost(sl.h_plans);
+    }
+    if (srv->pool) cudaFree(srv->pool);
+    delete srv;
+    if (e != cudaSuccess) return fail(PG_ERR_CUDA, "server destroy: %s", cudaGetErrorString(e));
     return PG_OK;
 }
 

@@ -32,6 +32,9 @@ struct OptParams {
     uint64_t part_w[kRP][kT - 1]; // new_i = x_i + w[i-1] x_0
 };
 
+// Records the text returned by pg_last_error() and passes `status` through.
+int set_error(int status, const char *fmt, ...);
+
 namespace host {
 uint64_t fp_add(uint64_t a, uint64_t b);
 uint64_t fp_sub(uint64_t a, uint64_t b);

@@ -81,3 +81,49 @@ def uniform01(seed: int, count: int) -> np.ndarray:
     """``count`` doubles uniform in [0, 1) from the top 53 bits of the words."""
     w = words(seed, count, bound=None)
     return (w >> np.uint64(11)).astype(np.float64) * (1.0 / (1 << 53))
+
+
+# ------------------------------------------------------------- torch version
+# The same streams computed with torch int64 arithmetic (wrapping multiply,
+# logical shifts emulated by masking), so large inputs can be generated where
+# they are used (for example directly in GPU memory).  Bit-identical to
+# words() / matrix() above.
+
+def _signed(v: int) -> int:
+    v &= 0xFFFFFFFFFFFFFFFF
+    return v - (1 << 64) if v >= (1 << 63) else v
+
+
+def _mix_t(z):
+    import torch  # noqa: F401
+    z = z ^ ((z >> 30) & ((1 << 34) - 1))
+    z = z * _signed(int(M1))
+    z = z ^ ((z >> 27) & ((1 << 37) - 1))
+    z = z * _signed(int(M2))
+    z = z ^ ((z >> 31) & ((1 << 33) - 1))
+    return z
+
+
+def words_torch(seed: int, count: int, start: int = 0, device="cpu", bound: int | None = FIELD_BOUND):
+    """torch.int64 tensor holding the bits of words(seed, count, start, bound)."""
+    import torch
+    key = int(_key(seed))
+    idx = torch.arange(start + 1, start + count + 1, dtype=torch.int64, device=device)
+    z = _mix_t(idx * _signed(int(GOLDEN)) + _signed(key))
+    if bound is not None:
+        b = _signed(bound)
+
+        def bad_of(t):
+            # unsigned t >= bound, on the int64 view of the words
+            if bound >= (1 << 63):
+                return (t < 0) & (t >= b)
+            return (t < 0) | (t >= b)
+        bad = bad_of(z)
+        while bool(bad.any()):
+            z = torch.where(bad, _mix_t(z), z)
+            bad = bad_of(z)
+    return z
+
+
+def matrix_torch(seed: int, rows: int, cols: int, device="cpu", bound: int | None = FIELD_BOUND):
+    return words_torch(seed, rows * cols, device=device, bound=bound).view(rows, cols)
