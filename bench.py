@@ -55,6 +55,7 @@ def parse_args():
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--max-log-n", type=int, default=22)
+    ap.add_argument("--server-order", type=int, default=0, help="tree order inside a served batch: 0 arrival, 1 most work first")
     return ap.parse_args()
 
 
@@ -442,7 +443,7 @@ def run_serve(args):
         rows_for(i)
     torch.cuda.synchronize()
     pool = int(min(torch.cuda.mem_get_info()[0] * 0.5, 64 << 30))
-    srv = pg.Server(pool_bytes=pool, max_batch=256, max_inflight=2, schedule={"order": 1})
+    srv = pg.Server(pool_bytes=pool, max_batch=256, max_inflight=2, schedule={"order": args.server_order})
     import time as _t
     lat = {}
     pending = []

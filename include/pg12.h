@@ -105,7 +105,10 @@ enum {
     PG_OP_REDUCE = 5,    /* (b * 2^64 + a) mod p           (Alg. 2, reduce_128_64)  */
     PG_OP_MUL_SMALL = 6, /* a * (b mod 2^8)                (mult_72)                */
     PG_OP_SBOX = 7,      /* a^7                            (Alg. 1 SBox)            */
-    PG_OP_DOT12 = 8      /* 12-term dot product, bench only (spmv/mmult rows)       */
+    PG_OP_DOT12 = 8,     /* 12-term dot product, bench only (spmv/mmult rows)       */
+    PG_OP_PIPE_IMAD = 9,       /* bench only: raw mad.lo.u32 throughput (IMAD)      */
+    PG_OP_PIPE_IMAD_WIDE = 10, /* bench only: raw mad.wide.u32 throughput           */
+    PG_OP_PIPE_IADD = 11       /* bench only: raw 32-bit add throughput             */
 };
 
 /* Library version, e.g. "pg12 1.0 sm_103a". */

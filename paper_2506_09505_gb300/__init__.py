@@ -103,7 +103,8 @@ SIGNATURES = {
                                       ctypes.POINTER(ctypes.c_double)]),
 }
 
-OPS = {"add": 1, "sub": 2, "mul": 3, "sqr": 4, "reduce": 5, "mul_small": 6, "sbox": 7, "dot12": 8}
+OPS = {"add": 1, "sub": 2, "mul": 3, "sqr": 4, "reduce": 5, "mul_small": 6, "sbox": 7, "dot12": 8,
+       "pipe_imad": 9, "pipe_imad_wide": 10, "pipe_iadd": 11}
 
 
 def lib_path() -> str:

@@ -65,11 +65,12 @@ __global__ void __launch_bounds__(256) k_field_bench(uint64_t *out, long long *c
 #pragma unroll
         for (int i = 0; i < 12; ++i) {
             if (OP == PG_OP_DOT12) {
-                // one 12-term lazy dot product per step, writing back to cell i
+                // one 12-term lazy dot product per step, writing back to cell i;
+                // every row has its own constants (no product repeats across rows)
                 Acc A;
                 acc_zero(A);
 #pragma unroll
-                for (int j = 0; j < 12; ++j) acc_mac(A, x[j], c + 977 * j);
+                for (int j = 0; j < 12; ++j) acc_mac(A, x[j], c + 977ull * j + 0x10001ull * i);
                 x[i] = acc_reduce(A);
             } else {
                 x[i] = apply(OP, x[i], x[(i + 1) % 12] ^ c);
@@ -84,6 +85,40 @@ __global__ void __launch_bounds__(256) k_field_bench(uint64_t *out, long long *c
     if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
 }
 
+// Raw pipe probes (bench only): 16 independent chains of one instruction
+// kind per thread, rotating operands so nothing folds at compile time.
+template <int KIND>
+__global__ void __launch_bounds__(256) k_pipe_bench(uint64_t *out, long long *cycles, int iters) {
+    uint32_t a[16];
+    uint64_t d[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        a[k] = 0x9E3779B9u * (threadIdx.x + 17 * k + 1) + blockIdx.x;
+        d[k] = a[k] * 0x2545F4914F6CDD1Dull;
+    }
+    const uint32_t b = 0x85EBCA6Bu ^ blockIdx.x;
+    __syncthreads();
+    const long long t0 = clock64();
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            if (KIND == 0) asm volatile("mad.lo.u32 %0, %0, %1, %2;" : "+r"(a[k]) : "r"(b), "r"(a[(k + 5) & 15]));
+            if (KIND == 1) asm volatile("mad.wide.u32 %0, %1, %2, %0;" : "+l"(d[k]) : "r"(a[k]), "r"(b));
+            if (KIND == 2) asm volatile("add.u32 %0, %0, %1;" : "+r"(a[k]) : "r"(a[(k + 3) & 15]));
+        }
+        if (KIND == 1) {
+#pragma unroll
+            for (int k = 0; k < 16; ++k) a[k] = (uint32_t)d[(k + 1) & 15];
+        }
+    }
+    const long long t1 = clock64();
+    uint64_t s = 0;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) s += a[k] + d[k];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+    if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
+}
+
 }  // namespace dev
 }  // namespace pg12
 
@@ -92,6 +127,43 @@ using namespace pg12;
 namespace {
 pg_status ops_fail(pg_status s, const char *what, cudaError_t e) {
     return (pg_status)set_error(s, "%s: %s", what, cudaGetErrorString(e));
+}
+
+template <int KIND>
+pg_status pipe_one(int sms, double *ops_per_s, double *ops_per_clk_sm) {
+    const int grid = sms * 4, threads = 256, iters = 400;
+    uint64_t *out = nullptr;
+    long long *cyc = nullptr;
+    cudaError_t e;
+    if ((e = cudaMalloc(&out, sizeof(uint64_t) * grid * threads)) != cudaSuccess) return ops_fail(PG_ERR_OOM, "malloc", e);
+    if ((e = cudaMalloc(&cyc, sizeof(long long) * grid)) != cudaSuccess) {
+        cudaFree(out);
+        return ops_fail(PG_ERR_OOM, "malloc", e);
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    dev::k_pipe_bench<KIND><<<grid, threads>>>(out, cyc, 2);
+    cudaEventRecord(e0);
+    dev::k_pipe_bench<KIND><<<grid, threads>>>(out, cyc, iters);
+    cudaEventRecord(e1);
+    e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    long long *h = new long long[grid];
+    cudaMemcpy(h, cyc, sizeof(long long) * grid, cudaMemcpyDeviceToHost);
+    double cmax = 0;
+    for (int i = 0; i < grid; ++i) cmax = h[i] > cmax ? (double)h[i] : cmax;
+    delete[] h;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(out);
+    cudaFree(cyc);
+    if (e != cudaSuccess) return ops_fail(PG_ERR_CUDA, "pipe kernel", e);
+    const double ops = (double)grid * threads * iters * 16;
+    if (ops_per_s) *ops_per_s = ops / (ms * 1e-3);
+    if (ops_per_clk_sm) *ops_per_clk_sm = cmax > 0 ? ops / (double)sms / cmax : 0.0;
+    return PG_OK;
 }
 
 template <int OP>
@@ -161,6 +233,9 @@ pg_status pg_field_bench(int op, double *ops_per_s, double *ops_per_clk_sm) {
         case PG_OP_MUL_SMALL: return bench_one<PG_OP_MUL_SMALL>(sms, ops_per_s, ops_per_clk_sm);
         case PG_OP_SBOX: return bench_one<PG_OP_SBOX>(sms, ops_per_s, ops_per_clk_sm);
         case PG_OP_DOT12: return bench_one<PG_OP_DOT12>(sms, ops_per_s, ops_per_clk_sm);
+        case PG_OP_PIPE_IMAD: return pipe_one<0>(sms, ops_per_s, ops_per_clk_sm);
+        case PG_OP_PIPE_IMAD_WIDE: return pipe_one<1>(sms, ops_per_s, ops_per_clk_sm);
+        case PG_OP_PIPE_IADD: return pipe_one<2>(sms, ops_per_s, ops_per_clk_sm);
         default: return (pg_status)set_error(PG_ERR_INVALID_ARG, "unknown op %d", op);
     }
 }

@@ -51,6 +51,8 @@ struct TreePlan {
     uint32_t leaf_task_begin;  // first global leaf-task index of this tree
     uint32_t counter_base;     // first arrival counter of this tree
     uint32_t vec16;            // rows can be read with 16-byte loads
+    uint32_t climb_limit;      // highest level the persistent kernel builds
+    uint32_t *done_flag;       // set to 1 once the root is stored (NULL = none)
     uint32_t level_counter[kMaxLevels];  // counter offset of level l's tasks (l >= 1)
 };
 
@@ -188,6 +190,16 @@ __device__ __forceinline__ void run_warp_task(const TreePlan &tp, uint32_t level
     st2(dst + 2, canon(slot[2 * S]), canon(slot[3 * S]));
 }
 
+// Completion flag of a tree: the root is stored by lane 0 of the warp that
+// built it; make its stores (and, through the climb's fences, the whole
+// tree) visible system-wide before raising the flag.
+__device__ __forceinline__ void signal_root(const TreePlan &tp, int lane) {
+    if (lane == 0 && tp.done_flag != nullptr) {
+        __threadfence_system();
+        *reinterpret_cast<volatile uint32_t *>(tp.done_flag) = 1u;
+    }
+}
+
 // Persistent Merkle kernel: every warp pulls leaf tasks from a global
 // counter (in order, so sibling subtrees finish close together), hashes
 // them, and announces each finished task to its parent's arrival counter.
@@ -219,7 +231,9 @@ __global__ void __launch_bounds__(S, PG12_MERKLE_MIN_BLOCKS * 256 / S) k_merkle(
         const uint32_t log_n = tp.log_n;
         uint64_t u = task - tp.leaf_task_begin;
         run_warp_task<S>(tp, 0, u, lane, slot);
-        for (uint32_t level = 1; level <= log_n; ++level) {
+        if (log_n == 0) signal_root(tp, lane);
+        const uint32_t top = log_n < tp.climb_limit ? log_n : tp.climb_limit;
+        for (uint32_t level = 1; level <= top; ++level) {
             const uint64_t below = n >> (level - 1);
             if (below > (uint64_t)kWarpNodes) {
                 // two child tasks: only the second to finish continues
@@ -235,6 +249,7 @@ __global__ void __launch_bounds__(S, PG12_MERKLE_MIN_BLOCKS * 256 / S) k_merkle(
             }
             u >>= 1;
             run_warp_task<S>(tp, level, u, lane, slot);
+            if (level == log_n) signal_root(tp, lane);
         }
     }
 }
@@ -281,6 +296,52 @@ __global__ void __launch_bounds__(kBlock) k_merkle_single(const TreePlan tp, uin
             run_warp_task<kBlock>(tp, level, u, lane, slot);
         }
     }
+}
+
+
+// Upper levels of a tree with the 16-lanes-per-state permutation: one group
+// per node of `level`, one launch per level.  Lanes 0..7 load the children,
+// lanes 0..3 store the digest.  Every lane reaches the shuffles (groups past
+// the level's end compute on a dummy node and skip the store).
+constexpr int kTopBlock = 256;
+__global__ void __launch_bounds__(kTopBlock) k_merkle_top(uint64_t *__restrict__ nodes, uint64_t n, uint32_t level) {
+    __shared__ __align__(16) DevConsts K;
+    load_consts(K);
+    const uint64_t count = n >> level;
+    const uint64_t gid = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 4;
+    const int l16 = threadIdx.x & 15;
+    const bool valid = gid < count;
+    const uint64_t node = valid ? gid : 0;
+    const uint64_t *kids = nodes + kDigest * (level_off(n, level - 1) + 2 * node);
+    uint64_t x = 0;
+    if (l16 < 2 * kDigest) {
+        asm volatile("ld.global.cg.u64 %0, [%1];" : "=l"(x) : "l"(kids + l16));
+    }
+    x = permute_wide(x, l16, 0xFFFFFFFFu, K);
+    if (valid && l16 < kDigest) nodes[kDigest * (level_off(n, level) + node) + l16] = canon(x);
+}
+
+// Leaf level of a small tree with the wide permutation: one group per row,
+// lanes 0..7 absorb the chunk words, lanes 8..11 carry the capacity.
+__global__ void __launch_bounds__(kTopBlock) k_merkle_top_leaf(const uint64_t *__restrict__ rows, uint64_t n,
+                                                               uint64_t w, uint64_t *__restrict__ nodes) {
+    __shared__ __align__(16) DevConsts K;
+    load_consts(K);
+    const uint64_t gid = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 4;
+    const int l16 = threadIdx.x & 15;
+    const bool valid = gid < n;
+    const uint64_t node = valid ? gid : 0;
+    const uint64_t *row = rows + node * w;
+    const uint64_t chunks = (w + kRate - 1) / kRate;
+    uint64_t x = 0;
+    for (uint64_t c = 0; c < chunks; ++c) {
+        if (l16 < kRate) {
+            const uint64_t k = c * kRate + l16;
+            x = k < w ? __ldg(row + k) : 0ull;
+        }
+        x = permute_wide(x, l16, 0xFFFFFFFFu, K);
+    }
+    if (valid && l16 < kDigest) nodes[kDigest * node + l16] = canon(x);
 }
 
 }  // namespace dev
@@ -332,6 +393,10 @@ namespace {
     } while (0)
 
 constexpr size_t kWorkspaceBytes = 32u << 20;  // tree plans + arrival counters
+#ifndef PG12_TOP_NODES
+#define PG12_TOP_NODES 32768
+#endif
+constexpr uint64_t kTopNodes = PG12_TOP_NODES;  // levels this small use the wide kernel
 constexpr size_t kPlanBytes = 4u << 20;        // first part: plans; rest: counters
 
 pg_status ensure_params() {
@@ -362,6 +427,8 @@ uint32_t plan_tree(dev::TreePlan &tp, const uint64_t *rows, uint64_t n, uint64_t
     tp.leaf_task_begin = leaf_task_begin;
     tp.counter_base = counter_base;
     tp.vec16 = ((w % 2) == 0 && (reinterpret_cast<uintptr_t>(rows) % 16) == 0) ? 1u : 0u;
+    tp.climb_limit = tp.log_n;
+    tp.done_flag = nullptr;
     n_counters = 0;
     for (uint32_t l = 0; l < (uint32_t)dev::kMaxLevels; ++l) tp.level_counter[l] = 0;
     for (uint32_t l = 1; l <= tp.log_n; ++l) {
@@ -528,6 +595,8 @@ struct ServerSlot {
     dev::TreePlan *h_plans = nullptr;  // pinned staging for the plan upload
     uint32_t *d_counters = nullptr;
     size_t counter_words = 0;
+    uint32_t *h_flags = nullptr;  // mapped pinned: per-request root-done flags
+    uint32_t *d_flags = nullptr;  // device view of h_flags
     std::vector<uint64_t> ids;
     bool busy = false;
 };
@@ -565,11 +634,24 @@ bool server_step(pg_server *s) {
     bool progress = false;
     for (auto &sl : s->slots) {
         if (!sl.busy) continue;
+        // requests whose root is already stored finish before their batch does
+        const double tf = s->now();
+        for (size_t k = 0; k < sl.ids.size(); ++k) {
+            if (reinterpret_cast<volatile uint32_t *>(sl.h_flags)[k] == 0u) continue;
+            auto &r = s->reqs[sl.ids[k]];
+            if (r.state == PG_REQ_RUNNING) {
+                r.state = PG_REQ_DONE;
+                r.t_done = tf;
+                --s->outstanding;
+                progress = true;
+            }
+        }
         const cudaError_t q = cudaEventQuery(sl.done);
         if (q == cudaErrorNotReady) continue;
         const double t = s->now();
         for (uint64_t id : sl.ids) {
             auto &r = s->reqs[id];
+            if (r.state != PG_REQ_RUNNING) continue;  // finished through its flag
             r.state = q == cudaSuccess ? PG_REQ_DONE : PG_REQ_FAILED;
             r.t_done = t;
             --s->outstanding;
@@ -624,6 +706,14 @@ bool server_step(pg_server *s) {
     pg_status st = plan_batch(trees.data(), trees.size(), &s->cfg.sched, plans, tasks, counters);
     cudaError_t e = cudaSuccess;
     if (st == PG_OK) {
+        // plans may be reordered: match each plan to its request by node buffer
+        for (size_t k = 0; k < take.size(); ++k) slot->h_flags[k] = 0u;
+        for (auto &pl : plans)
+            for (size_t k = 0; k < take.size(); ++k)
+                if (pl.nodes == trees[k].nodes) {
+                    pl.done_flag = slot->d_flags + k;
+                    break;
+                }
         std::memcpy(slot->h_plans, plans.data(), plans.size() * sizeof(dev::TreePlan));
         e = cudaMemcpyAsync(slot->d_plans, slot->h_plans, plans.size() * sizeof(dev::TreePlan),
                             cudaMemcpyHostToDevice, slot->stream);
@@ -714,6 +804,7 @@ pg_status pg_init(int device, const char *params_path) {
         dev::DevConsts dc;
         dev::make_dev_consts(g.opt, dc);
         PG_CUDA(cudaMemcpyToSymbol(dev::c_dev, &dc, sizeof(dc)));
+        PG_CUDA(cudaMemcpyToSymbol(dev::g_dev, &dc, sizeof(dc)));
     }
     PG_CUDA(cudaDeviceGetAttribute(&g.sms, cudaDevAttrMultiProcessorCount, device));
     PG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g.merkle_blocks_per_sm, dev::k_merkle<256>, 256, 0));
@@ -788,16 +879,39 @@ pg_status pg_merkle_build(const uint64_t *rows, size_t n_leaves, size_t width, u
     std::memset(&tp, 0, sizeof tp);
     uint32_t n_counters = 0;
     const uint32_t tasks = plan_tree(tp, rows, n_leaves, width, nodes, 0, 0, n_counters);
+    // levels with at most kTopNodes nodes are built by the low-latency
+    // 16-lanes-per-state kernel, one launch per level, after the persistent one
+    uint32_t first_top = tp.log_n + 1;
+    for (uint32_t l = 1; l <= tp.log_n; ++l)
+        if ((n_leaves >> l) <= (uint64_t)kTopNodes) {
+            first_top = l;
+            break;
+        }
+    tp.climb_limit = first_top - 1;
     const size_t counter_bytes = sizeof(uint32_t) * (1 + (size_t)n_counters);
     if (sizeof(tp) > kPlanBytes || counter_bytes > g.ws_bytes - kPlanBytes)
         return fail(PG_ERR_OOM, "workspace too small for %zu leaves", n_leaves);
     cudaStream_t st = as_stream(stream);
+    const bool small = (uint64_t)n_leaves <= kTopNodes;  // whole tree in the wide form
     auto *d_plan = reinterpret_cast<dev::TreePlan *>(g.ws);
     auto *d_counters = reinterpret_cast<uint32_t *>(g.ws + kPlanBytes);
-    PG_CUDA(cudaMemcpyAsync(d_plan, &tp, sizeof tp, cudaMemcpyHostToDevice, st));
-    PG_CUDA(cudaMemsetAsync(d_counters, 0, counter_bytes, st));
-    s = launch_merkle(nullptr, d_plan, 1u, tasks, d_counters, st);
-    if (s != PG_OK) return s;
+    if (small) {
+        const uint64_t threads = (uint64_t)n_leaves * 16;
+        const unsigned grid = (unsigned)((threads + dev::kTopBlock - 1) / dev::kTopBlock);
+        dev::k_merkle_top_leaf<<<grid, dev::kTopBlock, 0, st>>>(rows, (uint64_t)n_leaves, (uint64_t)width, nodes);
+        PG_CUDA(cudaGetLastError());
+    } else {
+        PG_CUDA(cudaMemcpyAsync(d_plan, &tp, sizeof tp, cudaMemcpyHostToDevice, st));
+        PG_CUDA(cudaMemsetAsync(d_counters, 0, counter_bytes, st));
+        s = launch_merkle(nullptr, d_plan, 1u, tasks, d_counters, st);
+        if (s != PG_OK) return s;
+    }
+    for (uint32_t l = first_top; l <= tp.log_n; ++l) {
+        const uint64_t threads = (n_leaves >> l) * 16;
+        const unsigned grid = (unsigned)((threads + dev::kTopBlock - 1) / dev::kTopBlock);
+        dev::k_merkle_top<<<grid, dev::kTopBlock, 0, st>>>(nodes, (uint64_t)n_leaves, l);
+        PG_CUDA(cudaGetLastError());
+    }
     if (root_out) {
         PG_CUDA(cudaMemcpyAsync(root_out, nodes + 4 * (2 * n_leaves - 2), 32, cudaMemcpyDeviceToHost, st));
         PG_CUDA(cudaStreamSynchronize(st));
@@ -968,6 +1082,7 @@ pg_status pg_server_create(const pg_server_config *cfg, pg_server **out) {
             if (sl.d_plans) cudaFree(sl.d_plans);
             if (sl.d_counters) cudaFree(sl.d_counters);
             if (sl.h_plans) cudaFreeHost(sl.h_plans);
+            if (sl.h_flags) cudaFreeHost(sl.h_flags);
         }
         if (srv->pool) cudaFree(srv->pool);
         delete srv;
@@ -985,6 +1100,9 @@ pg_status pg_server_create(const pg_server_config *cfg, pg_server **out) {
         if (e == cudaSuccess) e = cudaMalloc(&sl.d_plans, plan_bytes);
         if (e == cudaSuccess) e = cudaMalloc(&sl.d_counters, sizeof(uint32_t) * sl.counter_words);
         if (e == cudaSuccess) e = cudaMallocHost(&sl.h_plans, plan_bytes);
+        if (e == cudaSuccess)
+            e = cudaHostAlloc(&sl.h_flags, sizeof(uint32_t) * srv->cfg.max_batch, cudaHostAllocMapped);
+        if (e == cudaSuccess) e = cudaHostGetDevicePointer(&sl.d_flags, sl.h_flags, 0);
         if (e != cudaSuccess) return cleanup(fail(PG_ERR_OOM, "server stream buffers: %s", cudaGetErrorString(e)));
     }
     srv->worker = std::thread(server_loop, srv);
@@ -1076,6 +1194,7 @@ pg_status pg_server_destroy(pg_server *srv) {
         if (sl.d_plans) cudaFree(sl.d_plans);
         if (sl.d_counters) cudaFree(sl.d_counters);
         if (sl.h_plans) cudaFreeHost(sl.h_plans);
+        if (sl.h_flags) cudaFreeHost(sl.h_flags);
     }
     if (srv->pool) cudaFree(srv->pool);
     delete srv;

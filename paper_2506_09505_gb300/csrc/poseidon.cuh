@@ -65,18 +65,26 @@ __device__ __forceinline__ void sbox_phase(uint64_t *slot, int r) {
     }
 }
 
+#ifndef PG12_DENSE_ROWS
+#define PG12_DENSE_ROWS 1  // output rows per iteration of the dense loop (1 or 2)
+#endif
+
 template <int S>
 __device__ __forceinline__ void dense_phase(uint64_t *slot, int m) {
     uint64_t x[kT];
 #pragma unroll
     for (int j = 0; j < kT; ++j) x[j] = slot[j * S];
 #pragma unroll 1
-    for (int i = 0; i < kT; ++i) {
-        Acc A;
-        acc_zero(A);
+    for (int i = 0; i < kT; i += PG12_DENSE_ROWS) {
+        Acc A[PG12_DENSE_ROWS];
 #pragma unroll
-        for (int j = 0; j < kT; ++j) acc_mac(A, x[j], c_dev.mat[m][i][j]);
-        slot[i * S] = acc_reduce(A);
+        for (int k = 0; k < PG12_DENSE_ROWS; ++k) acc_zero(A[k]);
+#pragma unroll
+        for (int j = 0; j < kT; ++j)
+#pragma unroll
+            for (int k = 0; k < PG12_DENSE_ROWS; ++k) acc_mac(A[k], x[j], c_dev.mat[m][i + k][j]);
+#pragma unroll
+        for (int k = 0; k < PG12_DENSE_ROWS; ++k) slot[(i + k) * S] = acc_reduce(A[k]);
     }
 }
 
@@ -110,6 +118,74 @@ __device__ __forceinline__ void permute_slot(uint64_t *slot) {
         dense_phase<S>(slot, r == kRF / 2 - 1 ? 1 : 0);
         if (r == kRF / 2 - 1) partial_phase<S>(slot);
     }
+}
+
+
+// ------------------------------------------------------------ wide form
+// Sixteen lanes share one state: lane e < 12 holds cell x_e (lanes 12..15
+// carry zeros).  Used where few permutations are in flight (the top levels
+// of a tree), because its latency is about a tenth of the one-thread form.
+// Lanes index the constants by their own cell, so the kernels stage a copy
+// of the tables in shared memory (load_consts) and pass it in as K.
+__device__ __align__(16) DevConsts g_dev;
+static_assert(sizeof(DevConsts) % 16 == 0, "constant tables are copied in 16-byte pieces");
+
+// Block-wide copy of the constant tables into shared memory (16-byte loads).
+__device__ __forceinline__ void load_consts(DevConsts &dst) {
+    const uint4 *src = reinterpret_cast<const uint4 *>(&g_dev);
+    uint4 *d = reinterpret_cast<uint4 *>(&dst);
+    for (unsigned i = threadIdx.x; i < sizeof(DevConsts) / sizeof(uint4); i += blockDim.x) d[i] = __ldg(src + i);
+    __syncthreads();
+}
+
+__device__ __forceinline__ uint64_t add_weak(uint64_t a, uint64_t b) {
+    uint64_t s = a + b;
+    if (s < b) {
+        s += EPS;
+        if (s < EPS) s += EPS;  // second wrap (only when both inputs are >= p)
+    }
+    return s;
+}
+
+// `lane16` = lane index within its 16-lane group, `gmask` = the warp's active
+// mask; every lane of the group must execute this.  Latency is what matters
+// here, so the critical path is kept short: in a partial round the products
+// v_e x_e (e >= 1) and their butterfly sum do not wait for the S-box; only
+// v_0 x_0^7 is added after it.  Dense rows use two accumulators.
+__device__ __forceinline__ uint64_t permute_wide(uint64_t x, int lane16, unsigned gmask, const DevConsts &K) {
+    const int e = lane16 < kT ? lane16 : 0;
+    const bool live = lane16 < kT;
+    const int base = (threadIdx.x & 31) & ~15;
+#pragma unroll 1
+    for (int r = 0; r < kRF; ++r) {
+        x = live ? sbox(add_canon(x, K.full_rc[r][e])) : 0;
+        const int m = r == kRF / 2 - 1 ? 1 : 0;
+        Acc A, B;
+        acc_zero(A);
+        acc_zero(B);
+#pragma unroll
+        for (int j = 0; j < kT; j += 2) {
+            const uint64_t xa = __shfl_sync(gmask, x, base + j);
+            const uint64_t xb = __shfl_sync(gmask, x, base + j + 1);
+            acc_mac(A, xa, K.mat[m][e][j]);
+            acc_mac(B, xb, K.mat[m][e][j + 1]);
+        }
+        x = live ? add_weak(acc_reduce(A), acc_reduce(B)) : 0;
+        if (r == kRF / 2 - 1) {
+#pragma unroll 1
+            for (int q = 0; q < kRP; ++q) {
+                const uint64_t x0 = __shfl_sync(gmask, x, base);
+                const uint64_t y = sbox(add_canon(x0, K.part_rc[q]));
+                // sum of v_e x_e over e = 1..11 (independent of the S-box)
+                uint64_t t = (live && e != 0) ? mul(x, K.part_v[q][e]) : 0;
+#pragma unroll
+                for (int d = 8; d >= 1; d >>= 1) t = add_weak(t, __shfl_xor_sync(gmask, t, d));
+                x = e == 0 ? mul_add(K.part_v[q][0], y, t)
+                           : (live ? mul_add(K.part_w[q][e], y, x) : 0);
+            }
+        }
+    }
+    return x;
 }
 
 }  // namespace dev

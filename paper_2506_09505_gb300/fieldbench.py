@@ -9,9 +9,11 @@ import sys
 
 from . import field_bench, init, load
 
-OPS = ["add", "sub", "reduce", "sqr", "mul", "mul_small", "sbox", "dot12"]
+OPS = ["add", "sub", "reduce", "sqr", "mul", "mul_small", "sbox", "dot12",
+       "pipe_imad", "pipe_imad_wide", "pipe_iadd"]
 # 32-bit multiply results per operation (IMAD.WIDE counts 2)
-MUL_RESULTS = {"add": 0, "sub": 0, "reduce": 0, "sqr": 6, "mul": 8, "mul_small": 4, "sbox": 28, "dot12": 96}
+MUL_RESULTS = {"add": 0, "sub": 0, "reduce": 0, "sqr": 6, "mul": 8, "mul_small": 4, "sbox": 28, "dot12": 96,
+               "pipe_imad": 1, "pipe_imad_wide": 2, "pipe_iadd": 0}
 
 
 def main(argv=None):
