@@ -280,6 +280,33 @@ pg_status pg_field_eval(int op, const uint64_t *a, const uint64_t *b, uint64_t *
 pg_status pg_field_bench(int op, double *ops_per_s, double *ops_per_clk_sm);
 
 /*
+ * pg_merkle_open -- authentication paths of k leaves from a built tree
+ * (Sec. 2.4: the root commits to every leaf; a path is the sibling of each
+ * ancestor, from the leaf level up).
+ *   nodes     dev, level-major node array of a tree of n_leaves leaves.
+ *   indices   dev, k leaf indices (uint64, each < n_leaves, else the path is
+ *             filled with all-ones words).
+ *   paths     dev, k * log2(n_leaves) * 4 words; path q at
+ *             paths[q * log2(n_leaves) * 4 ..], level 0 sibling first.
+ * Asynchronous; pure gathers (no hashing).
+ */
+pg_status pg_merkle_open(const uint64_t *nodes, size_t n_leaves, const uint64_t *indices, size_t k,
+                         uint64_t *paths, void *stream);
+
+/*
+ * pg_merkle_verify -- recompute the root from each (leaf digest, index,
+ * path) with the permutation and compare it with `root`.
+ *   root       dev, 4 words.
+ *   leaves     dev, k * 4 words (leaf digests, level 0 of the tree).
+ *   indices    dev, k leaf indices.
+ *   paths      dev, as written by pg_merkle_open.
+ *   ok         dev, k bytes: 1 if the path reproduces the root, else 0.
+ * Needs pg_init().  Asynchronous.
+ */
+pg_status pg_merkle_verify(const uint64_t *root, size_t n_leaves, const uint64_t *leaves, const uint64_t *indices,
+                           size_t k, const uint64_t *paths, uint8_t *ok, void *stream);
+
+/*
  * pg_merkle_build_noalloc -- the same tree as pg_merkle_build (identical
  * output), for callers that cannot allocate device memory: code whose
  * allocator forbids cudaMalloc, or a host process that may only use the

@@ -97,6 +97,10 @@ SIGNATURES = {
     "pg_server_release": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64]),
     "pg_server_drain": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
     "pg_server_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "pg_merkle_open": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_size_t,
+                                      ctypes.c_void_p, ctypes.c_void_p]),
+    "pg_merkle_verify": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "pg_field_eval": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                      ctypes.c_size_t, ctypes.c_void_p]),
     "pg_field_bench": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
@@ -321,6 +325,28 @@ def batch_autotune(rows_list, nodes_list=None, stream=None):
     _check(load().pg_batch_autotune(arr, len(rows_list), _stream(stream), ctypes.byref(best),
                                     ctypes.byref(ms)))
     return best.as_dict(), float(ms.value)
+
+
+def merkle_open(nodes, n_leaves: int, indices, stream=None):
+    """Authentication paths (k, log2 N, 4) of the leaves in `indices` (int64 CUDA tensor)."""
+    import torch
+    depth = int(n_leaves).bit_length() - 1
+    k = indices.numel()
+    paths = torch.empty((k, depth, DIGEST), dtype=torch.int64, device=nodes.device)
+    _check(load().pg_merkle_open(_dev_ptr(nodes, "nodes"), n_leaves, _dev_ptr(indices, "indices"), k,
+                                 paths.data_ptr() if paths.numel() else None, _stream(stream)))
+    return paths
+
+
+def merkle_verify(root, n_leaves: int, leaves, indices, paths, stream=None):
+    """Bool tensor: does each (leaf digest, index, path) reproduce `root`?"""
+    import torch
+    k = indices.numel()
+    ok = torch.zeros(k, dtype=torch.uint8, device=indices.device)
+    _check(load().pg_merkle_verify(_dev_ptr(root, "root"), n_leaves, _dev_ptr(leaves, "leaves"),
+                                   _dev_ptr(indices, "indices"), k,
+                                   paths.data_ptr() if paths.numel() else None, ok.data_ptr(), _stream(stream)))
+    return ok.bool()
 
 
 def field_eval(op: str, a, b=None, stream=None):

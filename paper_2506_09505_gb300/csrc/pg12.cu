@@ -344,6 +344,57 @@ __global__ void __launch_bounds__(kTopBlock) k_merkle_top_leaf(const uint64_t *_
     if (valid && l16 < kDigest) nodes[kDigest * node + l16] = canon(x);
 }
 
+
+// Authentication paths: thread per (query, level) copies one sibling digest.
+__global__ void k_merkle_open(const uint64_t *__restrict__ nodes, uint64_t n, uint32_t depth,
+                              const uint64_t *__restrict__ idx, uint64_t k, uint64_t *__restrict__ paths) {
+    const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= k * depth) return;
+    const uint64_t q = t / depth;
+    const uint32_t l = (uint32_t)(t % depth);
+    const uint64_t leaf = idx[q];
+    uint64_t *dst = paths + kDigest * t;
+    if (leaf >= n) {
+        for (int i = 0; i < kDigest; ++i) dst[i] = ~0ull;
+        return;
+    }
+    const uint64_t sib = (leaf >> l) ^ 1ull;
+    const uint64_t *src = nodes + kDigest * (level_off(n, l) + sib);
+    for (int i = 0; i < kDigest; ++i) dst[i] = src[i];
+}
+
+// Path verification: one thread per query climbs log2(N) permutations.
+constexpr int kVerifyBlock = 128;
+__global__ void __launch_bounds__(kVerifyBlock) k_merkle_verify(const uint64_t *__restrict__ root, uint32_t depth,
+                                                                uint64_t n, const uint64_t *__restrict__ leaves,
+                                                                const uint64_t *__restrict__ idx, uint64_t k,
+                                                                const uint64_t *__restrict__ paths,
+                                                                uint8_t *__restrict__ ok) {
+    __shared__ uint64_t slots[kT * kVerifyBlock];
+    uint64_t *slot = slots + threadIdx.x;
+    const uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= k) return;
+    uint64_t cur[kDigest];
+    for (int i = 0; i < kDigest; ++i) cur[i] = leaves[kDigest * q + i];
+    uint64_t pos = idx[q];
+    const bool in_range = pos < n;
+    for (uint32_t l = 0; l < depth; ++l) {
+        const uint64_t *sib = paths + kDigest * (q * depth + l);
+        const bool right = pos & 1;
+        for (int i = 0; i < kDigest; ++i) {
+            slot[i * kVerifyBlock] = right ? sib[i] : cur[i];
+            slot[(kDigest + i) * kVerifyBlock] = right ? cur[i] : sib[i];
+            slot[(2 * kDigest + i) * kVerifyBlock] = 0;
+        }
+        permute_slot<kVerifyBlock>(slot);
+        for (int i = 0; i < kDigest; ++i) cur[i] = canon(slot[i * kVerifyBlock]);
+        pos >>= 1;
+    }
+    bool eq = in_range;
+    for (int i = 0; i < kDigest; ++i) eq = eq && (cur[i] == root[i]);
+    ok[q] = eq ? 1 : 0;
+}
+
 }  // namespace dev
 
 // ================================================================ host side
@@ -1199,6 +1250,35 @@ pg_status pg_server_destroy(pg_server *srv) {
     if (srv->pool) cudaFree(srv->pool);
     delete srv;
     if (e != cudaSuccess) return fail(PG_ERR_CUDA, "server destroy: %s", cudaGetErrorString(e));
+    return PG_OK;
+}
+
+pg_status pg_merkle_open(const uint64_t *nodes, size_t n_leaves, const uint64_t *indices, size_t k,
+                         uint64_t *paths, void *stream) {
+    if (!is_pow2(n_leaves)) return fail(PG_ERR_NOT_POW2, "n_leaves=%zu is not a power of two", n_leaves);
+    if (k == 0) return PG_OK;
+    if (!nodes || !indices || !paths) return fail(PG_ERR_INVALID_ARG, "NULL buffer");
+    const uint32_t depth = log2u(n_leaves);
+    if (depth == 0) return PG_OK;  // a one-leaf tree has empty paths
+    const uint64_t threads = (uint64_t)k * depth;
+    const unsigned grid = (unsigned)((threads + 255) / 256);
+    dev::k_merkle_open<<<grid, 256, 0, as_stream(stream)>>>(nodes, (uint64_t)n_leaves, depth, indices, (uint64_t)k, paths);
+    PG_CUDA(cudaGetLastError());
+    return PG_OK;
+}
+
+pg_status pg_merkle_verify(const uint64_t *root, size_t n_leaves, const uint64_t *leaves, const uint64_t *indices,
+                           size_t k, const uint64_t *paths, uint8_t *ok, void *stream) {
+    pg_status s = require_init();
+    if (s != PG_OK) return s;
+    if (!is_pow2(n_leaves)) return fail(PG_ERR_NOT_POW2, "n_leaves=%zu is not a power of two", n_leaves);
+    if (k == 0) return PG_OK;
+    if (!root || !leaves || !indices || !ok || (!paths && n_leaves > 1)) return fail(PG_ERR_INVALID_ARG, "NULL buffer");
+    const uint32_t depth = log2u(n_leaves);
+    const unsigned grid = (unsigned)((k + dev::kVerifyBlock - 1) / dev::kVerifyBlock);
+    dev::k_merkle_verify<<<grid, dev::kVerifyBlock, 0, as_stream(stream)>>>(root, depth, (uint64_t)n_leaves, leaves,
+                                                                            indices, (uint64_t)k, paths, ok);
+    PG_CUDA(cudaGetLastError());
     return PG_OK;
 }
 
