@@ -34,6 +34,9 @@ METRIC = "Poseidon-12 perms/s and 2^22-leaf Merkle build ms; % of IMAD roofline"
 # dense 12x12 MDS: S-boxes 118*(2*6+2*8) + full-round MDS 8*144*8 +
 # partial-round sparse layers 22*23*8.
 MUL_RESULTS_PER_PERM = 118 * (2 * 6 + 2 * 8) + 8 * 144 * 8 + 22 * 23 * 8
+# pg12_small: the seven full rounds with the 8-bit matrix take two 32x8-bit
+# IMAD.WIDE per term (4 results); round 3's transition matrix stays full width.
+MUL_RESULTS_PER_PERM_SMALL = 118 * (2 * 6 + 2 * 8) + 7 * 144 * 4 + 144 * 8 + 22 * 23 * 8
 IMAD_RESULTS_PER_CLK_SM = 64  # 32-bit multiply results per clock per SM
 
 
@@ -56,6 +59,7 @@ def parse_args():
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--max-log-n", type=int, default=22)
     ap.add_argument("--server-order", type=int, default=0, help="tree order inside a served batch: 0 arrival, 1 most work first")
+    ap.add_argument("--params", default=None, help="built-in parameter set: pg12_v1 (default) or pg12_small")
     return ap.parse_args()
 
 
@@ -214,7 +218,8 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
     pg.load(build_if_missing=True)
-    pg.init(local)
+    pg.init(local, args.params)
+    mul_per_perm = MUL_RESULTS_PER_PERM_SMALL if args.params == "pg12_small" else MUL_RESULTS_PER_PERM
 
     n, perms, name = workload(args.log_n, args.width)
     rows_np = pg_synth.matrix(pg_synth.config_seed(3) + rank, n, args.width)
@@ -281,7 +286,7 @@ def run_ours(args):
     sms = props.multi_processor_count
     max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     peak = IMAD_RESULTS_PER_CLK_SM * sms * max_mhz * 1e6 / 1e12  # T results/s
-    achieved = perms * MUL_RESULTS_PER_PERM / (ms / 1e3) / 1e12
+    achieved = perms * mul_per_perm / (ms / 1e3) / 1e12
     roofline = {
         "bound": "alu", "kernel": "k_merkle",
         "achieved": achieved, "peak": peak, "unit": "T mul32-results/s",
@@ -300,7 +305,8 @@ def run_ours(args):
         "dtype": "u64", "data": "synthetic",
         "config": {"workload": name, "leaves": n, "width": args.width, "perms_per_tree": perms,
                    "trees_per_gpu": 1, "parallelism": f"replicas x{world} (independent trees)",
-                   "l2": "inputs larger than L2 (rows 256 MiB/step at width 8), no flush"},
+                   "l2": "inputs larger than L2 (rows 256 MiB/step at width 8), no flush",
+                   "params": args.params or "pg12_v1"},
         "build_ms": ms, "build_ms_min": min(step_ms),
         "roofline": roofline, "e2e": e2e, "gpu_launches": args.steps, "clocks": clocks,
     }
@@ -317,12 +323,15 @@ def run_ours(args):
 
 
 # ------------------------------------------------------------ other workloads
+_ARGS = None
+
+
 def _device_setup():
     import torch
     import paper_2506_09505_gb300 as pg
     torch.cuda.set_device(0)
     pg.load(build_if_missing=True)
-    pg.init(0)
+    pg.init(0, _ARGS.params if _ARGS is not None else None)
     return torch, pg
 
 
@@ -350,8 +359,9 @@ def run_permute(args):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
     rate = n / (ms / 1e3)
-    ach = rate * MUL_RESULTS_PER_PERM
-    print(json.dumps({"workload": "permute 2^24 states in place", "metric": "perms/s", "value": rate,
+    ach = rate * (MUL_RESULTS_PER_PERM_SMALL if args.params == "pg12_small" else MUL_RESULTS_PER_PERM)
+    print(json.dumps({"workload": "permute 2^24 states in place", "params": args.params or "pg12_v1",
+                      "metric": "perms/s", "value": rate,
                       "ms_per_step": ms, "steps": args.steps, "kernel": "k_permute",
                       "roofline": {"bound": "alu", "achieved": ach / 1e12, "peak": _peak_results_per_s() / 1e12,
                                    "unit": "T mul32-results/s", "frac": ach / _peak_results_per_s()}}), flush=True)
@@ -514,7 +524,9 @@ def run_serve(args):
 
 
 def main():
+    global _ARGS
     args = parse_args()
+    _ARGS = args
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "permute":

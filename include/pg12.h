@@ -118,15 +118,30 @@ const char *pg_version(void);
 const char *pg_last_error(void);
 
 /*
- * pg_init -- select `device`, build parameter set pg12_v1 on the host and
- * upload the optimised-form constants (Alg. 1) to the device.
+ * pg_init -- select `device`, build the parameter set on the host and upload
+ * the optimised-form constants (Alg. 1) to the device.
  *   device       CUDA ordinal.
- *   params_path  must be NULL (built-in pg12_v1); any other value returns
- *                PG_ERR_PARAMS.
- * Idempotent for the same device.  Synchronous.  Allocates the workspace
- * used by pg_merkle_build / pg_merkle_build_batch.
+ *   params_path  name of a built-in parameter set: NULL or "pg12_v1" (Cauchy
+ *                MDS, the default) or "pg12_small" (circulant MDS with 8-bit
+ *                entries, Table 1's mult_72 / mmult_4x12_8 shape); anything
+ *                else returns PG_ERR_PARAMS.
+ * Idempotent for the same device (a different set name switches the active
+ * set, see pg_params_select).  Synchronous.  Allocates the workspace used by
+ * pg_merkle_build / pg_merkle_build_batch.
  */
 pg_status pg_init(int device, const char *params_path);
+
+/*
+ * pg_params_select -- make a built-in parameter set ("pg12_v1" or NULL,
+ * "pg12_small") the active one for every later call of this process.  Works
+ * without a GPU (host generation only); after pg_init it also reloads the
+ * device constants.  Device work in flight keeps the constants it started
+ * with only if the caller synchronises before switching.
+ */
+pg_status pg_params_select(const char *name);
+
+/* Name of the active parameter set. */
+const char *pg_params_name(void);
 
 /* Release the workspace.  Safe to call when not initialised. */
 pg_status pg_shutdown(void);

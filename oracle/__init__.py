@@ -66,6 +66,8 @@ def _load():
         "orc_auth_path": (i, [_u64p, sz, sz, _u64p]),
         "orc_root_from_path": (None, [_u64p, _u64p, _u64p, sz, _u64p, sz, _u64p]),
         "orc_count_singular_minors": (ctypes.c_long, [_u64p, ctypes.POINTER(ctypes.c_long)]),
+        "orc_is_mds": (i, [_u64p]),
+        "orc_params_generate_small": (i, [_u64p, _u64p, _u64p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -162,6 +164,27 @@ def params():
             a.setflags(write=False)
         _PARAMS = (rc, mds, xs, ys, int(redraws))
     return _PARAMS
+
+
+_PARAMS_SMALL = None
+
+
+def params_small():
+    """Parameter set pg12_small: (rc[30,12], mds[12,12], first circulant row[12], candidate index)."""
+    global _PARAMS_SMALL
+    if _PARAMS_SMALL is None:
+        rc = np.zeros((ROUNDS, T), dtype=np.uint64)
+        mds = np.zeros((T, T), dtype=np.uint64)
+        row = np.zeros(T, dtype=np.uint64)
+        cand = _load().orc_params_generate_small(_ptr(rc), _ptr(mds), _ptr(row))
+        for a in (rc, mds, row):
+            a.setflags(write=False)
+        _PARAMS_SMALL = (rc, mds, row, int(cand))
+    return _PARAMS_SMALL
+
+
+def is_mds(m) -> bool:
+    return bool(_load().orc_is_mds(_ptr(_u64(m))))
 
 
 def _rc_mds(rc, mds):

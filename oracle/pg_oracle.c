@@ -473,3 +473,54 @@ long orc_count_singular_minors(const uint64_t *m, long *checked) {
     if (checked) *checked = total;
     return bad;
 }
+
+/* ------------------------------------------- small-entry parameter set */
+
+/* Same as orc_count_singular_minors but stops at the first singular minor,
+ * visiting minors by increasing size.  Returns 1 if every minor is
+ * nonsingular (the matrix is MDS), else 0. */
+int orc_is_mds(const uint64_t *m) {
+    uint64_t a[12 * 12];
+    for (int k = 1; k <= 12; k++) {
+        for (int rs = 1; rs < (1 << 12); rs++) {
+            if (__builtin_popcount((unsigned)rs) != k) continue;
+            int rows[12], nr = 0;
+            for (int i = 0; i < 12; i++)
+                if (rs >> i & 1) rows[nr++] = i;
+            for (int cs = 1; cs < (1 << 12); cs++) {
+                if (__builtin_popcount((unsigned)cs) != k) continue;
+                int cols[12], nc = 0;
+                for (int j = 0; j < 12; j++)
+                    if (cs >> j & 1) cols[nc++] = j;
+                for (int i = 0; i < k; i++)
+                    for (int j = 0; j < k; j++) a[i * 12 + j] = m[rows[i] * 12 + cols[j]];
+                if (orc_small_det(a, k) == 0) return 0;
+            }
+        }
+    }
+    return 1;
+}
+
+/* Parameter set pg12_small: the round constants of pg12_v1 (the first 360
+ * field elements of the same Grain stream), and a circulant MDS matrix with
+ * 8-bit entries -- the matrix shape whose products Table 1's mult_72 and
+ * mmult_4x12_8 serve.  After the round constants the stream yields
+ * candidates of twelve 64-bit words each; entry c_i = 1 + (word mod 255)
+ * (so 1..255) and M[i][j] = c[(j - i) mod 12].  The first candidate whose
+ * matrix is MDS is taken.  Writes rc[360], mds[144], row[12]; returns the
+ * index of the accepted candidate. */
+int orc_params_generate_small(uint64_t *rc, uint64_t *mds, uint64_t *row) {
+    orc_grain g;
+    orc_grain_init(&g, 1, 0, 64, ORC_T, ORC_RF, ORC_RP);
+    for (int k = 0; k < ORC_ROUNDS * ORC_T; k++) rc[k] = orc_grain_field(&g);
+    for (int cand = 0;; cand++) {
+        uint64_t c[12];
+        for (int i = 0; i < 12; i++) c[i] = 1 + orc_grain_word(&g, 64) % 255;
+        for (int i = 0; i < 12; i++)
+            for (int j = 0; j < 12; j++) mds[i * 12 + j] = c[((j - i) % 12 + 12) % 12];
+        if (orc_is_mds(mds)) {
+            memcpy(row, c, sizeof c);
+            return cand;
+        }
+    }
+}

@@ -72,6 +72,8 @@ SIGNATURES = {
     "pg_version": (ctypes.c_char_p, []),
     "pg_last_error": (ctypes.c_char_p, []),
     "pg_init": (ctypes.c_int, [ctypes.c_int, ctypes.c_char_p]),
+    "pg_params_select": (ctypes.c_int, [ctypes.c_char_p]),
+    "pg_params_name": (ctypes.c_char_p, []),
     "pg_shutdown": (ctypes.c_int, []),
     "pg_params_export": (ctypes.c_int, [_u64p, _u64p]),
     "pg_params_export_optimized": (ctypes.c_int, [_u64p] * 6),
@@ -172,8 +174,17 @@ def params_export_optimized():
 
 # ------------------------------------------------------------ device calls
 
-def init(device: int = 0) -> None:
-    _check(load().pg_init(int(device), None))
+def init(device: int = 0, params: str | None = None) -> None:
+    """pg_init on `device` with a built-in parameter set (None = pg12_v1)."""
+    _check(load().pg_init(int(device), params.encode() if params else None))
+
+
+def params_select(name: str | None) -> None:
+    _check(load().pg_params_select(name.encode() if name else None))
+
+
+def params_name() -> str:
+    return load().pg_params_name().decode()
 
 
 def shutdown() -> None:

@@ -114,6 +114,84 @@ void generate_plain(PlainParams &pp) {
     }
 }
 
+// --------------------------------------------- small-entry parameter set
+namespace {
+// Goldilocks product without a division: 2^64 = 2^32 - 1, 2^96 = -1.
+inline uint64_t fast_mul(uint64_t a, uint64_t b) {
+    const unsigned __int128 r = (unsigned __int128)a * b;
+    const uint64_t lo = (uint64_t)r, hi = (uint64_t)(r >> 64);
+    const uint64_t hl = hi & 0xFFFFFFFFull, hh = hi >> 32;
+    uint64_t t = lo - hh;
+    if (lo < hh) t -= 0xFFFFFFFFull;
+    const uint64_t u = (hl << 32) - hl;
+    uint64_t v = t + u;
+    if (v < u) v += 0xFFFFFFFFull;
+    return v >= kP ? v - kP : v;
+}
+inline uint64_t fast_sub(uint64_t a, uint64_t b) { return a >= b ? a - b : a + (kP - b); }
+
+// Nonsingular k x k submatrix?  Elimination by cross-multiplication
+// (row_j <- p * row_j - f * row_pivot), so no inverses are needed.
+bool minor_nonsingular(uint64_t (&a)[kT][kT], int k) {
+    for (int c = 0; c < k; ++c) {
+        int piv = -1;
+        for (int r = c; r < k; ++r)
+            if (a[r][c]) { piv = r; break; }
+        if (piv < 0) return false;
+        if (piv != c)
+            for (int j = c; j < k; ++j) std::swap(a[piv][j], a[c][j]);
+        const uint64_t p = a[c][c];
+        for (int r = c + 1; r < k; ++r) {
+            const uint64_t f = a[r][c];
+            if (!f) continue;
+            for (int j = c; j < k; ++j) a[r][j] = fast_sub(fast_mul(p, a[r][j]), fast_mul(f, a[c][j]));
+        }
+    }
+    return true;
+}
+
+// MDS test of a circulant matrix: every square submatrix nonsingular.  A
+// submatrix and its copy shifted by s along both axes are equal, so only row
+// sets that contain row 0 are visited.
+bool circulant_is_mds(const uint64_t (&m)[kT][kT]) {
+    uint64_t a[kT][kT];
+    for (int k = 1; k <= kT; ++k) {
+        for (int rs = 1; rs < (1 << kT); rs += 2) {  // row 0 always present
+            if (__builtin_popcount((unsigned)rs) != k) continue;
+            int rows[kT], nr = 0;
+            for (int i = 0; i < kT; ++i)
+                if (rs >> i & 1) rows[nr++] = i;
+            for (int cs = 1; cs < (1 << kT); ++cs) {
+                if (__builtin_popcount((unsigned)cs) != k) continue;
+                int cols[kT], nc = 0;
+                for (int j = 0; j < kT; ++j)
+                    if (cs >> j & 1) cols[nc++] = j;
+                for (int i = 0; i < k; ++i)
+                    for (int j = 0; j < k; ++j) a[i][j] = m[rows[i]][cols[j]];
+                if (!minor_nonsingular(a, k)) return false;
+            }
+        }
+    }
+    return true;
+}
+}  // namespace
+
+int generate_small(PlainParams &pp, uint32_t row[kT]) {
+    Grain g(1, 0, 64, kT, kRF, kRP);
+    for (int r = 0; r < kRounds; ++r)
+        for (int i = 0; i < kT; ++i) pp.rc[r][i] = g.element();
+    for (int cand = 0;; ++cand) {
+        uint32_t c[kT];
+        for (auto &v : c) v = (uint32_t)(1 + g.word64() % 255);
+        for (int i = 0; i < kT; ++i)
+            for (int j = 0; j < kT; ++j) pp.mds[i][j] = c[((j - i) % kT + kT) % kT];
+        if (circulant_is_mds(pp.mds)) {
+            for (int i = 0; i < kT; ++i) row[i] = c[i];
+            return cand;
+        }
+    }
+}
+
 // ------------------------------------------------------- sparse rewrite
 namespace {
 using Mat = std::vector<std::vector<uint64_t>>;

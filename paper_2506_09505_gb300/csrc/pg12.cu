@@ -91,7 +91,7 @@ __device__ __forceinline__ void load_chunk(const uint64_t *row, uint64_t w, uint
 
 // Overwrite-mode sponge over one row in the thread's state slot; returns
 // with the (weak) final state in the slot.
-template <int S>
+template <int S, int MDS>
 __device__ __forceinline__ void sponge_slot(const uint64_t *row, uint64_t w, bool vec16, uint64_t *slot) {
 #pragma unroll
     for (int i = kRate; i < kT; ++i) slot[i * S] = 0;
@@ -101,13 +101,14 @@ __device__ __forceinline__ void sponge_slot(const uint64_t *row, uint64_t w, boo
         load_chunk(row, w, c, vec16, ch);
 #pragma unroll
         for (int i = 0; i < kRate; ++i) slot[i * S] = ch[i];
-        permute_slot<S>(slot);
+        permute_slot<S, MDS>(slot);
     }
 }
 
 // ------------------------------------------------------------- kernels
 constexpr int kSmallBlock = 128;
 
+template <int MDS>
 __global__ void __launch_bounds__(kSmallBlock) k_permute(uint64_t *__restrict__ st, uint64_t n, int vec16) {
     __shared__ uint64_t slots[kT * kSmallBlock];
     uint64_t *slot = slots + threadIdx.x;
@@ -126,7 +127,7 @@ __global__ void __launch_bounds__(kSmallBlock) k_permute(uint64_t *__restrict__ 
 #pragma unroll
             for (int i = 0; i < kT; ++i) slot[i * kSmallBlock] = p[i];
         }
-        permute_slot<kSmallBlock>(slot);
+        permute_slot<kSmallBlock, MDS>(slot);
         if (vec16) {
 #pragma unroll
             for (int i = 0; i < kT; i += 2) st2(p + i, canon(slot[i * kSmallBlock]), canon(slot[(i + 1) * kSmallBlock]));
@@ -137,13 +138,14 @@ __global__ void __launch_bounds__(kSmallBlock) k_permute(uint64_t *__restrict__ 
     }
 }
 
+template <int MDS>
 __global__ void __launch_bounds__(kSmallBlock) k_hash_rows(const uint64_t *__restrict__ rows, uint64_t n,
                                                            uint64_t w, int vec16, uint64_t *__restrict__ out) {
     __shared__ uint64_t slots[kT * kSmallBlock];
     uint64_t *slot = slots + threadIdx.x;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
-        sponge_slot<kSmallBlock>(rows + r * w, w, vec16 != 0, slot);
+        sponge_slot<kSmallBlock, MDS>(rows + r * w, w, vec16 != 0, slot);
         st2(out + kDigest * r, canon(slot[0]), canon(slot[kSmallBlock]));
         st2(out + kDigest * r + 2, canon(slot[2 * kSmallBlock]), canon(slot[3 * kSmallBlock]));
     }
@@ -154,7 +156,7 @@ __global__ void __launch_bounds__(kSmallBlock) k_hash_rows(const uint64_t *__res
 // level l-1 -- in the lane's shared-memory state slot (stride S = threads
 // per block).  Both cases feed one permutation call site, so the kernel holds
 // a single copy of the permutation code.
-template <int S>
+template <int S, int MDS>
 __device__ __forceinline__ void run_warp_task(const TreePlan &tp, uint32_t level, uint64_t u, int lane,
                                               uint64_t *slot) {
     const uint64_t n = tp.n_leaves;
@@ -183,7 +185,7 @@ __device__ __forceinline__ void run_warp_task(const TreePlan &tp, uint32_t level
                 slot[(k + 1) * S] = b;
             }
         }
-        permute_slot<S>(slot);
+        permute_slot<S, MDS>(slot);
     }
     uint64_t *dst = tp.nodes + kDigest * (level_off(n, level) + i);
     st2(dst, canon(slot[0]), canon(slot[S]));
@@ -207,7 +209,7 @@ __device__ __forceinline__ void signal_root(const TreePlan &tp, int lane) {
 // the parent and keeps climbing; the first arriver goes back for a new leaf
 // task.  Levels with at most 32 nodes have a single task and are climbed
 // without counters.  No block-wide barrier and no waiting anywhere.
-template <int S>
+template <int S, int MDS>
 __global__ void __launch_bounds__(S, PG12_MERKLE_MIN_BLOCKS * 256 / S) k_merkle(const TreePlan *__restrict__ plans, uint32_t n_trees,
                                              uint32_t total_tasks, uint32_t *__restrict__ counters,
                                              uint32_t *__restrict__ next_task) {
@@ -230,7 +232,7 @@ __global__ void __launch_bounds__(S, PG12_MERKLE_MIN_BLOCKS * 256 / S) k_merkle(
         const uint64_t n = tp.n_leaves;
         const uint32_t log_n = tp.log_n;
         uint64_t u = task - tp.leaf_task_begin;
-        run_warp_task<S>(tp, 0, u, lane, slot);
+        run_warp_task<S, MDS>(tp, 0, u, lane, slot);
         if (log_n == 0) signal_root(tp, lane);
         const uint32_t top = log_n < tp.climb_limit ? log_n : tp.climb_limit;
         for (uint32_t level = 1; level <= top; ++level) {
@@ -248,7 +250,7 @@ __global__ void __launch_bounds__(S, PG12_MERKLE_MIN_BLOCKS * 256 / S) k_merkle(
                 __syncwarp();
             }
             u >>= 1;
-            run_warp_task<S>(tp, level, u, lane, slot);
+            run_warp_task<S, MDS>(tp, level, u, lane, slot);
             if (level == log_n) signal_root(tp, lane);
         }
     }
@@ -265,6 +267,7 @@ constexpr uint64_t kNoAllocMaxLeaves = 1ull << 22;
 constexpr size_t kNoAllocWords = (size_t)(kNoAllocMaxLeaves / kWarpNodes);  // task counter + arrival counters
 static __device__ __align__(256) uint32_t g_noalloc_scratch[kNoAllocWords];
 
+template <int MDS>
 __global__ void __launch_bounds__(kBlock) k_merkle_single(const TreePlan tp, uint32_t total_tasks,
                                                           uint32_t *__restrict__ counters,
                                                           uint32_t *__restrict__ next_task) {
@@ -279,7 +282,7 @@ __global__ void __launch_bounds__(kBlock) k_merkle_single(const TreePlan tp, uin
         task = __shfl_sync(full, task, 0);
         if (task >= total_tasks) return;
         uint64_t u = task;
-        run_warp_task<kBlock>(tp, 0, u, lane, slot);
+        run_warp_task<kBlock, MDS>(tp, 0, u, lane, slot);
         for (uint32_t level = 1; level <= tp.log_n; ++level) {
             if ((n >> (level - 1)) > (uint64_t)kWarpNodes) {
                 __threadfence();
@@ -293,7 +296,7 @@ __global__ void __launch_bounds__(kBlock) k_merkle_single(const TreePlan tp, uin
                 __syncwarp();
             }
             u >>= 1;
-            run_warp_task<kBlock>(tp, level, u, lane, slot);
+            run_warp_task<kBlock, MDS>(tp, level, u, lane, slot);
         }
     }
 }
@@ -365,6 +368,7 @@ __global__ void k_merkle_open(const uint64_t *__restrict__ nodes, uint64_t n, ui
 
 // Path verification: one thread per query climbs log2(N) permutations.
 constexpr int kVerifyBlock = 128;
+template <int MDS>
 __global__ void __launch_bounds__(kVerifyBlock) k_merkle_verify(const uint64_t *__restrict__ root, uint32_t depth,
                                                                 uint64_t n, const uint64_t *__restrict__ leaves,
                                                                 const uint64_t *__restrict__ idx, uint64_t k,
@@ -386,7 +390,7 @@ __global__ void __launch_bounds__(kVerifyBlock) k_merkle_verify(const uint64_t *
             slot[(kDigest + i) * kVerifyBlock] = right ? cur[i] : sib[i];
             slot[(2 * kDigest + i) * kVerifyBlock] = 0;
         }
-        permute_slot<kVerifyBlock>(slot);
+        permute_slot<kVerifyBlock, MDS>(slot);
         for (int i = 0; i < kDigest; ++i) cur[i] = canon(slot[i * kVerifyBlock]);
         pos >>= 1;
     }
@@ -402,13 +406,16 @@ namespace {
 
 struct Context {
     bool params_ready = false;
+    int params_set = 0;  // 0 = pg12_v1, 1 = pg12_small
+    int params_gen = 1;  // bumped whenever the active set changes
+    uint32_t small_row[kT] = {};
     PlainParams plain;
     OptParams opt;
     bool init = false;
     int device = -1;
     int sms = 0;
-    int merkle_blocks_per_sm = 0;      // k_merkle<256>
-    int merkle128_blocks_per_sm = 0;   // k_merkle<128>
+    int merkle_blocks_per_sm = 0;      // k_merkle<256, *> (both matrix kinds: minimum)
+    int merkle128_blocks_per_sm = 0;   // k_merkle<128, *>
     int permute_blocks_per_sm = 0;
     uint8_t *ws = nullptr;  // device workspace
     size_t ws_bytes = 0;
@@ -452,7 +459,8 @@ constexpr size_t kPlanBytes = 4u << 20;        // first part: plans; rest: count
 
 pg_status ensure_params() {
     if (g.params_ready) return PG_OK;
-    host::generate_plain(g.plain);
+    if (g.params_set == 1) host::generate_small(g.plain, g.small_row);
+    else host::generate_plain(g.plain);
     if (!host::derive_optimized(g.plain, g.opt))
         return fail(PG_ERR_PARAMS, "parameter set pg12_v1: sparse rewrite failed (singular block)");
     g.params_ready = true;
@@ -557,10 +565,14 @@ pg_status launch_merkle(const pg_schedule *sched, const dev::TreePlan *d_plans, 
     const uint32_t cap = (uint32_t)(g.sms * bps);
     const unsigned grid = want < cap ? want : cap;
     if (grid == 0) return PG_OK;
-    if (block == 128)
-        dev::k_merkle<128><<<grid, 128, 0, st>>>(d_plans, n_trees, tasks, d_counters + 1, d_counters);
-    else
-        dev::k_merkle<256><<<grid, 256, 0, st>>>(d_plans, n_trees, tasks, d_counters + 1, d_counters);
+    const bool small = g.params_set == 1;
+    if (block == 128) {
+        if (small) dev::k_merkle<128, dev::kMdsSmall><<<grid, 128, 0, st>>>(d_plans, n_trees, tasks, d_counters + 1, d_counters);
+        else dev::k_merkle<128, dev::kMdsFull><<<grid, 128, 0, st>>>(d_plans, n_trees, tasks, d_counters + 1, d_counters);
+    } else {
+        if (small) dev::k_merkle<256, dev::kMdsSmall><<<grid, 256, 0, st>>>(d_plans, n_trees, tasks, d_counters + 1, d_counters);
+        else dev::k_merkle<256, dev::kMdsFull><<<grid, 256, 0, st>>>(d_plans, n_trees, tasks, d_counters + 1, d_counters);
+    }
     PG_CUDA(cudaGetLastError());
     return PG_OK;
 }
@@ -840,13 +852,40 @@ pg_status pg_params_export_optimized(uint64_t *full_rc, uint64_t *mds, uint64_t 
     return PG_OK;
 }
 
-pg_status pg_init(int device, const char *params_path) {
+pg_status pg_params_select(const char *name) {
     std::lock_guard<std::mutex> lk(g_mu);
-    if (params_path != nullptr) return fail(PG_ERR_PARAMS, "only the built-in parameter set pg12_v1 is supported");
-    if (g.init && g.device == device) return PG_OK;
-    if (g.init) return fail(PG_ERR_INVALID_ARG, "already initialised on device %d", g.device);
+    int want = 0;
+    if (name == nullptr || std::strcmp(name, "pg12_v1") == 0) want = 0;
+    else if (std::strcmp(name, "pg12_small") == 0) want = 1;
+    else return fail(PG_ERR_PARAMS, "unknown parameter set '%s' (built-in: pg12_v1, pg12_small)", name);
+    if (want != g.params_set) {
+        g.params_set = want;
+        g.params_ready = false;
+        ++g.params_gen;
+    }
     pg_status s = ensure_params();
     if (s != PG_OK) return s;
+    if (g.init) {
+        PG_CUDA(cudaSetDevice(g.device));
+        dev::DevConsts dc;
+        dev::make_dev_consts(g.opt, dc);
+        PG_CUDA(cudaMemcpyToSymbol(dev::c_dev, &dc, sizeof(dc)));
+        PG_CUDA(cudaMemcpyToSymbol(dev::g_dev, &dc, sizeof(dc)));
+    }
+    return PG_OK;
+}
+
+const char *pg_params_name(void) { return g.params_set == 1 ? "pg12_small" : "pg12_v1"; }
+
+pg_status pg_init(int device, const char *params_path) {
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        if (g.init && g.device != device) return fail(PG_ERR_INVALID_ARG, "already initialised on device %d", g.device);
+    }
+    pg_status s = pg_params_select(params_path);
+    if (s != PG_OK) return s;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (g.init) return PG_OK;  // constants of the selected set already loaded
     int ndev = 0;
     PG_CUDA(cudaGetDeviceCount(&ndev));
     if (device < 0 || device >= ndev) return fail(PG_ERR_INVALID_ARG, "device %d out of range (%d)", device, ndev);
@@ -858,9 +897,18 @@ pg_status pg_init(int device, const char *params_path) {
         PG_CUDA(cudaMemcpyToSymbol(dev::g_dev, &dc, sizeof(dc)));
     }
     PG_CUDA(cudaDeviceGetAttribute(&g.sms, cudaDevAttrMultiProcessorCount, device));
-    PG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g.merkle_blocks_per_sm, dev::k_merkle<256>, 256, 0));
-    PG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g.merkle128_blocks_per_sm, dev::k_merkle<128>, 128, 0));
-    PG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g.permute_blocks_per_sm, dev::k_permute, dev::kSmallBlock, 0));
+    {
+        int a = 0, b = 0, c = 0, d = 0, e = 0, f = 0;
+        PG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, dev::k_merkle<256, dev::kMdsFull>, 256, 0));
+        PG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, dev::k_merkle<256, dev::kMdsSmall>, 256, 0));
+        PG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, dev::k_merkle<128, dev::kMdsFull>, 128, 0));
+        PG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d, dev::k_merkle<128, dev::kMdsSmall>, 128, 0));
+        PG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&e, dev::k_permute<dev::kMdsFull>, dev::kSmallBlock, 0));
+        PG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&f, dev::k_permute<dev::kMdsSmall>, dev::kSmallBlock, 0));
+        g.merkle_blocks_per_sm = a < b ? a : b;
+        g.merkle128_blocks_per_sm = c < d ? c : d;
+        g.permute_blocks_per_sm = e < f ? e : f;
+    }
     if (g.merkle_blocks_per_sm < 1 || g.merkle128_blocks_per_sm < 1 || g.permute_blocks_per_sm < 1)
         return fail(PG_ERR_CUDA, "kernels cannot be resident (occupancy 0)");
     void *ws = nullptr;
@@ -894,7 +942,8 @@ pg_status pg_permute_batch(uint64_t *states, size_t n, void *stream) {
     const uint64_t want = (n + 127) / 128;
     const uint64_t cap = (uint64_t)g.sms * g.permute_blocks_per_sm * 8;
     const unsigned grid = (unsigned)(want < cap ? want : cap);
-    dev::k_permute<<<grid, 128, 0, as_stream(stream)>>>(states, (uint64_t)n, vec16);
+    if (g.params_set == 1) dev::k_permute<dev::kMdsSmall><<<grid, 128, 0, as_stream(stream)>>>(states, (uint64_t)n, vec16);
+    else dev::k_permute<dev::kMdsFull><<<grid, 128, 0, as_stream(stream)>>>(states, (uint64_t)n, vec16);
     PG_CUDA(cudaGetLastError());
     return PG_OK;
 }
@@ -911,7 +960,10 @@ pg_status pg_hash_rows(const uint64_t *rows, size_t n_rows, size_t width, uint64
     const uint64_t want = (n_rows + 127) / 128;
     const uint64_t cap = (uint64_t)g.sms * g.permute_blocks_per_sm * 8;
     const unsigned grid = (unsigned)(want < cap ? want : cap);
-    dev::k_hash_rows<<<grid, 128, 0, as_stream(stream)>>>(rows, (uint64_t)n_rows, (uint64_t)width, vec16, digests);
+    if (g.params_set == 1)
+        dev::k_hash_rows<dev::kMdsSmall><<<grid, 128, 0, as_stream(stream)>>>(rows, (uint64_t)n_rows, (uint64_t)width, vec16, digests);
+    else
+        dev::k_hash_rows<dev::kMdsFull><<<grid, 128, 0, as_stream(stream)>>>(rows, (uint64_t)n_rows, (uint64_t)width, vec16, digests);
     PG_CUDA(cudaGetLastError());
     return PG_OK;
 }
@@ -1276,8 +1328,12 @@ pg_status pg_merkle_verify(const uint64_t *root, size_t n_leaves, const uint64_t
     if (!root || !leaves || !indices || !ok || (!paths && n_leaves > 1)) return fail(PG_ERR_INVALID_ARG, "NULL buffer");
     const uint32_t depth = log2u(n_leaves);
     const unsigned grid = (unsigned)((k + dev::kVerifyBlock - 1) / dev::kVerifyBlock);
-    dev::k_merkle_verify<<<grid, dev::kVerifyBlock, 0, as_stream(stream)>>>(root, depth, (uint64_t)n_leaves, leaves,
-                                                                            indices, (uint64_t)k, paths, ok);
+    if (g.params_set == 1)
+        dev::k_merkle_verify<dev::kMdsSmall><<<grid, dev::kVerifyBlock, 0, as_stream(stream)>>>(root, depth, (uint64_t)n_leaves,
+                                                                                             leaves, indices, (uint64_t)k, paths, ok);
+    else
+        dev::k_merkle_verify<dev::kMdsFull><<<grid, dev::kVerifyBlock, 0, as_stream(stream)>>>(root, depth, (uint64_t)n_leaves,
+                                                                                            leaves, indices, (uint64_t)k, paths, ok);
     PG_CUDA(cudaGetLastError());
     return PG_OK;
 }
@@ -1294,6 +1350,7 @@ pg_status pg_merkle_build_noalloc(const uint64_t *rows, size_t n_leaves, size_t 
     static uint32_t *scratch_ptr[kMaxDevices];
     static int blocks_per_sm[kMaxDevices];
     static int sm_count[kMaxDevices];
+    static int consts_gen[kMaxDevices];  // parameter-set generation loaded on each device
     if (!rows || !nodes) return fail(PG_ERR_INVALID_ARG, "rows or nodes is NULL");
     if (width == 0) return fail(PG_ERR_INVALID_ARG, "width must be >= 1");
     if (!is_pow2(n_leaves)) return fail(PG_ERR_NOT_POW2, "n_leaves=%zu is not a power of two", n_leaves);
@@ -1307,15 +1364,18 @@ pg_status pg_merkle_build_noalloc(const uint64_t *rows, size_t n_leaves, size_t 
     if (device < 0 || device >= kMaxDevices) return fail(PG_ERR_INVALID_ARG, "device %d out of range", device);
     {
         std::lock_guard<std::mutex> lk(g_mu);
-        if (scratch_ptr[device] == nullptr) {
+        if (scratch_ptr[device] == nullptr || consts_gen[device] != g.params_gen) {
             pg_status s = ensure_params();
             if (s != PG_OK) return s;
             dev::DevConsts dc;
             dev::make_dev_consts(g.opt, dc);
             PG_CUDA(cudaMemcpyToSymbol(dev::c_dev, &dc, sizeof(dc)));
+            consts_gen[device] = g.params_gen;
             PG_CUDA(cudaDeviceGetAttribute(&sm_count[device], cudaDevAttrMultiProcessorCount, device));
-            PG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm[device], dev::k_merkle_single,
-                                                                  dev::kBlock, 0));
+            int oa = 0, ob = 0;
+            PG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oa, dev::k_merkle_single<dev::kMdsFull>, dev::kBlock, 0));
+            PG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ob, dev::k_merkle_single<dev::kMdsSmall>, dev::kBlock, 0));
+            blocks_per_sm[device] = oa < ob ? oa : ob;
             if (blocks_per_sm[device] < 1) return fail(PG_ERR_CUDA, "k_merkle_single cannot be resident");
             void *p = nullptr;
             PG_CUDA(cudaGetSymbolAddress(&p, dev::g_noalloc_scratch));
@@ -1336,7 +1396,8 @@ pg_status pg_merkle_build_noalloc(const uint64_t *rows, size_t n_leaves, size_t 
     const uint32_t want = (tasks + warps_per_block - 1) / warps_per_block;
     const uint32_t cap = (uint32_t)(sm_count[device] * blocks_per_sm[device]);
     const unsigned grid = want < cap ? want : cap;
-    dev::k_merkle_single<<<grid, dev::kBlock, 0, st>>>(tp, tasks, scratch + 1, scratch);
+    if (g.params_set == 1) dev::k_merkle_single<dev::kMdsSmall><<<grid, dev::kBlock, 0, st>>>(tp, tasks, scratch + 1, scratch);
+    else dev::k_merkle_single<dev::kMdsFull><<<grid, dev::kBlock, 0, st>>>(tp, tasks, scratch + 1, scratch);
     PG_CUDA(cudaGetLastError());
     return PG_OK;
 }

@@ -42,6 +42,10 @@ uint64_t fp_mul(uint64_t a, uint64_t b);
 uint64_t fp_pow(uint64_t a, uint64_t e);
 uint64_t fp_inv(uint64_t a);
 void generate_plain(PlainParams &pp);
+// pg12_small: pg12_v1's round constants and a circulant MDS matrix with
+// 8-bit entries; `row` receives its first row.  Returns the accepted
+// candidate's index.
+int generate_small(PlainParams &pp, uint32_t row[kT]);
 bool derive_optimized(const PlainParams &pp, OptParams &op);
 }  // namespace host
 

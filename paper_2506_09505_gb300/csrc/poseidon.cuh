@@ -32,6 +32,9 @@ struct DevConsts {
     uint64_t part_rc[kRP];
     uint64_t part_v[kRP][kT];
     uint64_t part_w[kRP][kT];  // entry 0 unused (keeps rows 16-byte aligned)
+    uint32_t small_mat[kT][kT];  // M again when its entries fit 8 bits
+    uint32_t small;              // 1: full rounds other than round 3 use small_mat
+    uint32_t pad[3];
 };
 
 // One copy per translation unit that includes this header; filled by
@@ -39,6 +42,14 @@ struct DevConsts {
 __constant__ __align__(16) DevConsts c_dev;
 
 inline void make_dev_consts(const OptParams &op, DevConsts &dc) {
+    bool small = true;
+    for (int i = 0; i < kT; ++i)
+        for (int j = 0; j < kT; ++j) {
+            small = small && op.mds[i][j] < 256;
+            dc.small_mat[i][j] = (uint32_t)(op.mds[i][j] & 0xFFu);
+        }
+    dc.small = small ? 1u : 0u;
+    dc.pad[0] = dc.pad[1] = dc.pad[2] = 0;
     for (int r = 0; r < kRF; ++r)
         for (int i = 0; i < kT; ++i) dc.full_rc[r][i] = op.full_rc[r][i];
     for (int i = 0; i < kT; ++i)
@@ -88,6 +99,36 @@ __device__ __forceinline__ void dense_phase(uint64_t *slot, int m) {
     }
 }
 
+// Dense layer of an MDS matrix with 8-bit entries (Table 1's mmult_4x12_8):
+// x_j * m for m < 2^8 is two 32x8-bit products; twelve of them fit 64 bits,
+// so both halves accumulate through the IMAD.WIDE addend with no carries and
+// one fold per output.
+__device__ __forceinline__ uint64_t madw(uint32_t a, uint32_t b, uint64_t c) {
+    uint64_t d;
+    asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
+    return d;
+}
+
+template <int S>
+__device__ __forceinline__ void dense_small_phase(uint64_t *slot) {
+    uint64_t x[kT];
+#pragma unroll
+    for (int j = 0; j < kT; ++j) x[j] = slot[j * S];
+#pragma unroll 1
+    for (int i = 0; i < kT; ++i) {
+        uint64_t lo = 0, hi = 0;  // sums of x_j.lo * m_ij and x_j.hi * m_ij (< 2^44 each)
+#pragma unroll
+        for (int j = 0; j < kT; ++j) {
+            const uint32_t m = c_dev.small_mat[i][j];
+            lo = madw(lo32(x[j]), m, lo);
+            hi = madw(hi32(x[j]), m, hi);
+        }
+        // value = lo + hi * 2^32 < 2^77
+        const u128 v = (u128)lo + ((u128)hi << 32);
+        slot[i * S] = reduce128(v);
+    }
+}
+
 template <int S>
 __device__ __forceinline__ void partial_phase(uint64_t *slot) {
     uint64_t x[kT];
@@ -109,13 +150,19 @@ __device__ __forceinline__ void partial_phase(uint64_t *slot) {
     for (int j = 0; j < kT; ++j) slot[j * S] = x[j];
 }
 
+// Matrix kinds the kernels are compiled for: the full-width Cauchy matrix
+// of pg12_v1 and the 8-bit circulant of pg12_small (chosen on the host from
+// the active parameter set, so each kernel carries only its own code).
+enum MdsKind { kMdsFull = 0, kMdsSmall = 1 };
+
 // The permutation on the state in `slot` (weak words in, weak words out).
-template <int S>
+template <int S, int MDS = kMdsFull>
 __device__ __forceinline__ void permute_slot(uint64_t *slot) {
 #pragma unroll 1
     for (int r = 0; r < kRF; ++r) {
         sbox_phase<S>(slot, r);
-        dense_phase<S>(slot, r == kRF / 2 - 1 ? 1 : 0);
+        if (MDS == kMdsSmall && r != kRF / 2 - 1) dense_small_phase<S>(slot);
+        else dense_phase<S>(slot, r == kRF / 2 - 1 ? 1 : 0);
         if (r == kRF / 2 - 1) partial_phase<S>(slot);
     }
 }

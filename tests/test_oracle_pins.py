@@ -409,3 +409,27 @@ def test_merkle_subtree_split_recombines():
 def test_merkle_rejects_non_power_of_two():
     with pytest.raises(ValueError):
         oracle.merkle_build(pg_synth.matrix(30, 3, 8))
+
+
+# ------------------------------------------------ small-entry parameter set
+
+def test_small_set_is_circulant_mds_with_v1_constants():
+    rc, mds, row, cand = oracle.params_small()
+    assert (rc == oracle.params()[0]).all()
+    assert all(1 <= int(v) <= 255 for v in row)
+    for i in range(12):
+        for j in range(12):
+            assert int(mds[i, j]) == int(row[(j - i) % 12])
+    assert cand >= 0
+    assert oracle.is_mds(mds)
+
+
+def test_is_mds_rejects_a_singular_minor():
+    # a circulant whose first row repeats with period 6 has equal rows i, i+6
+    row = [3, 5, 7, 11, 13, 17] * 2
+    m = np.array([[row[(j - i) % 12] for j in range(12)] for i in range(12)], dtype=np.uint64)
+    assert not oracle.is_mds(m)
+    # and a 2x2 minor that vanishes: [[2, 4], [1, 2]] inside an otherwise random matrix
+    r = pg_synth.matrix(0x77, 12, 12)
+    r[0, 0], r[0, 1], r[1, 0], r[1, 1] = 2, 4, 1, 2
+    assert not oracle.is_mds(r)

@@ -66,3 +66,30 @@ def test_optimised_constants_canonical(lib):
         assert (a < np.uint64(P)).all(), name
     # the dense full-round matrix is the plain MDS matrix
     assert (op["mds"] == oracle.params()[1]).all()
+
+
+def test_small_set_matches_oracle_and_optimised_form(lib):
+    try:
+        pg.params_select("pg12_small")
+        assert pg.params_name() == "pg12_small"
+        rc, mds = pg.params_export()
+        orc_rc, orc_mds, row, _ = oracle.params_small()
+        assert (rc == orc_rc).all() and (mds == orc_mds).all()
+        # circulant with 8-bit entries
+        for i in range(12):
+            for j in range(12):
+                assert int(mds[i, j]) == int(row[(j - i) % 12]) and 1 <= int(mds[i, j]) <= 255
+        op = pg.params_export_optimized()
+        st = pg_synth.matrix(0xAC, 16, 12)
+        want = oracle.permute(st, orc_rc, orc_mds)
+        for k in range(st.shape[0]):
+            assert _opt_permute(st[k], op) == [int(v) for v in want[k]]
+    finally:
+        pg.params_select(None)
+    assert pg.params_name() == "pg12_v1"
+
+
+def test_unknown_set_rejected(lib):
+    with pytest.raises(pg.PGError) as e:
+        pg.params_select("nope")
+    assert e.value.status == 6
