@@ -38,6 +38,10 @@ MUL_RESULTS_PER_PERM = 118 * (2 * 6 + 2 * 8) + 8 * 144 * 8 + 22 * 23 * 8
 # IMAD.WIDE per term (4 results); round 3's transition matrix stays full width.
 MUL_RESULTS_PER_PERM_SMALL = 118 * (2 * 6 + 2 * 8) + 7 * 144 * 4 + 144 * 8 + 22 * 23 * 8
 IMAD_RESULTS_PER_CLK_SM = 64  # 32-bit multiply results per clock per SM
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_merkle
+# launch, from one ncu capture of the current kernel on that workload
+# (params, log2 leaves, width); other workloads report null.
+K_MERKLE_TRAFFIC = {("pg12_v1", 22, 8): 274_836_992 + 224_612_096}
 
 
 def parse_args():
@@ -245,11 +249,15 @@ def run_ours(args):
     sampler = ClockSampler(gpu_id)
     time.sleep(0.4)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    # per-kernel CUDA events, recorded by the library on the launching stream
+    pg.profile_enable(True)
     ev[0].record(stream)
     for k in range(args.steps):
         pg.merkle_build(rows, nodes)
         ev[k + 1].record(stream)
     barrier()
+    kernels = pg.profile_read()
+    pg.profile_enable(False)
     clocks = sampler.stop()
     step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
     total_ms = ev[0].elapsed_time(ev[-1])
@@ -286,13 +294,21 @@ def run_ours(args):
     sms = props.multi_processor_count
     max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     peak = IMAD_RESULTS_PER_CLK_SM * sms * max_mhz * 1e6 / 1e12  # T results/s
-    achieved = perms * mul_per_perm / (ms / 1e3) / 1e12
+    dropped = kernels.pop("_dropped", 0)
+    km = kernels["k_merkle"]
+    km_ms = km["total_ms"] / km["launches"]          # average k_merkle launch, event-timed
+    km_perms = km["perms"] // km["launches"]         # its permutations per launch
+    achieved = km_perms * mul_per_perm / (km_ms / 1e3) / 1e12
+    tot_kernel_ms = sum(v["total_ms"] for v in kernels.values())
     roofline = {
         "bound": "alu", "kernel": "k_merkle",
         "achieved": achieved, "peak": peak, "unit": "T mul32-results/s",
         "frac": achieved / peak,
         "peak_basis": f"{IMAD_RESULTS_PER_CLK_SM} x {sms} SMs x {max_mhz:.0f} MHz (sm_max_mhz)",
-        "traffic": None,
+        "traffic": K_MERKLE_TRAFFIC.get((args.params or "pg12_v1", args.log_n, args.width)),
+        "launch_ms": km_ms, "perms_per_launch": km_perms,
+        "mul32_results_per_launch": km_perms * mul_per_perm,
+        "step_frac": perms * mul_per_perm / (ms / 1e3) / 1e12 / peak,
         "algorithmic_bytes_per_launch": int(rows_np.nbytes + 32 * (2 * n - 1)),
     }
     if clocks and clocks.get("sm_mhz"):
@@ -308,7 +324,11 @@ def run_ours(args):
                    "l2": "inputs larger than L2 (rows 256 MiB/step at width 8), no flush",
                    "params": args.params or "pg12_v1"},
         "build_ms": ms, "build_ms_min": min(step_ms),
-        "roofline": roofline, "e2e": e2e, "gpu_launches": args.steps, "clocks": clocks,
+        "roofline": roofline, "e2e": e2e,
+        "gpu_launches": sum(v["launches"] for v in kernels.values()) + dropped,
+        "kernels": {k: {"launches": v["launches"], "ms_per_launch": v["total_ms"] / v["launches"],
+                        "share": v["total_ms"] / tot_kernel_ms} for k, v in kernels.items()},
+        "clocks": clocks,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, cores, log_s, dt, sp = oracle_rate(args.width, args.cpu_seconds)

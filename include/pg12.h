@@ -345,6 +345,40 @@ pg_status pg_merkle_verify(const uint64_t *root, size_t n_leaves, const uint64_t
 pg_status pg_merkle_build_noalloc(const uint64_t *rows, size_t n_leaves, size_t width, uint64_t *nodes,
                                   void *stream);
 
+/*
+ * Launch timing (the cudaEvent side of the paper's hardware-counter
+ * measurements, Sec. 4.1-4.2): when enabled, every kernel launch the library
+ * makes (and every pg_batch_graph_launch) is bracketed by a pair of CUDA
+ * events recorded on the launching stream.  Launches made while a stream is
+ * being captured are not recorded.  At most 65,536 launches are held;
+ * further ones are counted as dropped.
+ *
+ * pg_profile_enable -- on != 0 starts recording, 0 stops it; either way the
+ * records held so far are discarded.  Host-synchronous with those records'
+ * events.  Never fails.
+ */
+typedef struct pg_kernel_time {
+    char name[32];     /* kernel name: "k_merkle", "k_merkle_top", ..., "batch_graph" */
+    uint64_t launches; /* launches recorded */
+    uint64_t perms;    /* permutations those launches performed */
+    double total_ms;   /* sum of their event-timed durations */
+} pg_kernel_time;
+
+pg_status pg_profile_enable(int on);
+
+/*
+ * pg_profile_read -- waits for the recorded launches to finish, sums them
+ * per kernel into out[0 .. *n_out) (kernels with no launch are left out) and
+ * clears the records (recording stays as it was).
+ *   out      host array of cap entries, or NULL to only count.
+ *   n_out    host, receives the number of kernels with launches.
+ *   dropped  host or NULL, receives the launches not recorded since the
+ *            last enable/read because the record store was full.
+ * PG_ERR_INVALID_ARG if out is non-NULL and cap < *n_out (the first cap
+ * entries are still written); PG_ERR_CUDA if an event could not be read.
+ */
+pg_status pg_profile_read(pg_kernel_time *out, size_t cap, size_t *n_out, uint64_t *dropped);
+
 #ifdef __cplusplus
 }
 #endif

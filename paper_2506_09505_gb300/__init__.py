@@ -65,6 +65,12 @@ class RequestInfo(ctypes.Structure):
                 ("launch_s", ctypes.c_double), ("done_s", ctypes.c_double), ("nodes", ctypes.c_void_p)]
 
 
+class KernelTime(ctypes.Structure):
+    """pg_kernel_time of include/pg12.h."""
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_uint64), ("perms", ctypes.c_uint64),
+                ("total_ms", ctypes.c_double)]
+
+
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
 
 # name -> (restype, argtypes) for every symbol declared in include/pg12.h
@@ -107,6 +113,9 @@ SIGNATURES = {
                                      ctypes.c_size_t, ctypes.c_void_p]),
     "pg_field_bench": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                       ctypes.POINTER(ctypes.c_double)]),
+    "pg_profile_enable": (ctypes.c_int, [ctypes.c_int]),
+    "pg_profile_read": (ctypes.c_int, [ctypes.POINTER(KernelTime), ctypes.c_size_t,
+                                       ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_uint64)]),
 }
 
 OPS = {"add": 1, "sub": 2, "mul": 3, "sqr": 4, "reduce": 5, "mul_small": 6, "sbox": 7, "dot12": 8,
@@ -374,6 +383,24 @@ def field_bench(op: str):
     rate, per_clk = ctypes.c_double(), ctypes.c_double()
     _check(load().pg_field_bench(OPS[op], ctypes.byref(rate), ctypes.byref(per_clk)))
     return rate.value, per_clk.value
+
+
+def profile_enable(on: bool = True) -> None:
+    """Start (or stop) event timing of every launch; discards earlier records."""
+    _check(load().pg_profile_enable(1 if on else 0))
+
+
+def profile_read() -> dict:
+    """Per-kernel launches, permutations and summed event time since the last
+    enable/read: {name: {"launches", "perms", "total_ms"}} plus "_dropped"."""
+    n, dropped = ctypes.c_size_t(), ctypes.c_uint64()
+    cap = 16
+    arr = (KernelTime * cap)()
+    _check(load().pg_profile_read(arr, cap, ctypes.byref(n), ctypes.byref(dropped)))
+    out = {arr[k].name.decode(): {"launches": int(arr[k].launches), "perms": int(arr[k].perms),
+                                  "total_ms": float(arr[k].total_ms)} for k in range(n.value)}
+    out["_dropped"] = int(dropped.value)
+    return out
 
 
 class Server:

@@ -2,13 +2,15 @@
 //
 //   k_permute   Alg. 1 on a batch of independent states, one thread each.
 //   k_hash_rows Sec. 2.4 sponge (rate 8, capacity 4, overwrite mode) per row.
-//   k_merkle    Sec. 4.2 tree build as one persistent launch: blocks pull
-//               leaf tiles from a global counter, hash a tile of rows and
-//               fuse the next levels in shared memory; the block that
-//               completes the last child tile of a parent tile (an atomic
-//               arrival counter, never a spin) goes on to build that parent
-//               tile, so the upper levels start as soon as their subtree is
-//               ready instead of after a grid-wide barrier.
+//   k_merkle    Sec. 4.2 tree build as one persistent launch: warps pull
+//               32-leaf tasks from a global counter and hash those rows; the
+//               warp that completes the second of two sibling 32-node groups
+//               (an atomic arrival counter, never a spin) goes on to hash
+//               their 32 parents, so the upper levels start as soon as their
+//               subtree is ready instead of after a grid-wide barrier.
+//   k_merkle_top / k_merkle_top_leaf
+//               the levels with few nodes, 16 lanes per state (latency form).
+//   k_merkle_open / k_merkle_verify  authentication paths (Sec. 2.4).
 #include "pg12.h"
 #include "pg12_internal.h"
 #include "poseidon.cuh"
@@ -16,6 +18,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -457,6 +460,101 @@ constexpr size_t kWorkspaceBytes = 32u << 20;  // tree plans + arrival counters
 constexpr uint64_t kTopNodes = PG12_TOP_NODES;  // levels this small use the wide kernel
 constexpr size_t kPlanBytes = 4u << 20;        // first part: plans; rest: counters
 
+// ------------------------------------------------------------ launch timing
+// Optional per-kernel timing (pg_profile_enable / pg_profile_read): a pair of
+// CUDA events is recorded on the launching stream around each launch and
+// resolved when the records are read.  Launches inside a stream capture are
+// not recorded (the graph launch is, as one entry).
+enum KernelId {
+    kIdMerkle, kIdMerkleTop, kIdMerkleTopLeaf, kIdPermute, kIdHashRows, kIdOpen, kIdVerify, kIdSingle,
+    kIdGraph, kIdCount
+};
+const char *const kKernelNames[kIdCount] = {"k_merkle",      "k_merkle_top",    "k_merkle_top_leaf",
+                                            "k_permute",     "k_hash_rows",     "k_merkle_open",
+                                            "k_merkle_verify", "k_merkle_single", "batch_graph"};
+constexpr size_t kProfMaxRecords = 1u << 16;
+
+struct ProfRecord {
+    int kid;
+    int device;
+    uint64_t perms;
+    cudaEvent_t a, b;
+};
+
+struct Profiler {
+    std::mutex mu;
+    std::atomic<bool> on{false};
+    std::vector<ProfRecord> recs;
+    std::vector<std::pair<int, cudaEvent_t>> spare;  // (device, event)
+    uint64_t dropped = 0;
+
+    cudaEvent_t take(int device) {  // mu held
+        for (size_t k = spare.size(); k-- > 0;)
+            if (spare[k].first == device) {
+                cudaEvent_t e = spare[k].second;
+                spare.erase(spare.begin() + (long)k);
+                return e;
+            }
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        return e;
+    }
+};
+Profiler g_prof;
+
+// Records one launch (the kernel launched between construction and
+// destruction) when profiling is on.
+class ProfScope {
+  public:
+    ProfScope(int kid, cudaStream_t st, uint64_t perms) : st_(st) {
+        if (!g_prof.on.load(std::memory_order_relaxed)) return;
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
+        int device = 0;
+        if (cudaGetDevice(&device) != cudaSuccess) return;
+        std::lock_guard<std::mutex> lk(g_prof.mu);
+        if (g_prof.recs.size() >= kProfMaxRecords) {
+            ++g_prof.dropped;
+            return;
+        }
+        rec_ = ProfRecord{kid, device, perms, g_prof.take(device), nullptr};
+        if (rec_.a) rec_.b = g_prof.take(device);
+        if (!rec_.a || !rec_.b || cudaEventRecord(rec_.a, st) != cudaSuccess) {
+            if (rec_.a) g_prof.spare.emplace_back(device, rec_.a);
+            if (rec_.b) g_prof.spare.emplace_back(device, rec_.b);
+            return;
+        }
+        active_ = true;
+    }
+    ~ProfScope() {
+        if (!active_) return;
+        const bool ok = cudaEventRecord(rec_.b, st_) == cudaSuccess;
+        std::lock_guard<std::mutex> lk(g_prof.mu);
+        if (ok) {
+            g_prof.recs.push_back(rec_);
+        } else {
+            g_prof.spare.emplace_back(rec_.device, rec_.a);
+            g_prof.spare.emplace_back(rec_.device, rec_.b);
+        }
+    }
+    ProfScope(const ProfScope &) = delete;
+    ProfScope &operator=(const ProfScope &) = delete;
+
+  private:
+    cudaStream_t st_;
+    ProfRecord rec_{};
+    bool active_ = false;
+};
+
+// Permutations of a whole tree: ceil(w/8) per leaf plus one per inner node.
+uint64_t tree_perms(uint64_t n, uint64_t w) { return n * ((w + kRate - 1) / kRate) + (n - 1); }
+
+uint64_t batch_perms(const pg_tree *trees, size_t n_trees) {
+    uint64_t p = 0;
+    for (size_t k = 0; k < n_trees; ++k) p += tree_perms(trees[k].n_leaves, trees[k].width);
+    return p;
+}
+
 pg_status ensure_params() {
     if (g.params_ready) return PG_OK;
     if (g.params_set == 1) host::generate_small(g.plain, g.small_row);
@@ -555,7 +653,7 @@ pg_status plan_batch(const pg_tree *trees, size_t n_trees, const pg_schedule *sc
 
 // Launch the persistent Merkle kernel for `tasks` leaf tasks.
 pg_status launch_merkle(const pg_schedule *sched, const dev::TreePlan *d_plans, uint32_t n_trees, uint32_t tasks,
-                        uint32_t *d_counters, cudaStream_t st) {
+                        uint32_t *d_counters, cudaStream_t st, uint64_t perms) {
     const uint32_t block = (sched && sched->block == 128) ? 128u : 256u;
     const int occ = block == 128 ? g.merkle128_blocks_per_sm : g.merkle_blocks_per_sm;
     int bps = occ;
@@ -566,6 +664,7 @@ pg_status launch_merkle(const pg_schedule *sched, const dev::TreePlan *d_plans, 
     const unsigned grid = want < cap ? want : cap;
     if (grid == 0) return PG_OK;
     const bool small = g.params_set == 1;
+    ProfScope prof(kIdMerkle, st, perms);
     if (block == 128) {
         if (small) dev::k_merkle<128, dev::kMdsSmall><<<grid, 128, 0, st>>>(d_plans, n_trees, tasks, d_counters + 1, d_counters);
         else dev::k_merkle<128, dev::kMdsFull><<<grid, 128, 0, st>>>(d_plans, n_trees, tasks, d_counters + 1, d_counters);
@@ -587,6 +686,7 @@ struct pg_batch_graph {
     size_t plan_bytes;
     uint32_t n_trees, tasks;
     uint64_t counters;
+    uint64_t perms;
     cudaGraph_t graph;
     cudaGraphExec_t exec;
     cudaStream_t capture;
@@ -784,7 +884,7 @@ bool server_step(pg_server *s) {
             e = cudaMemsetAsync(slot->d_counters, 0, sizeof(uint32_t) * (1 + (size_t)counters), slot->stream);
         if (e == cudaSuccess)
             st = launch_merkle(&s->cfg.sched, slot->d_plans, (uint32_t)plans.size(), tasks, slot->d_counters,
-                               slot->stream);
+                               slot->stream, batch_perms(trees.data(), trees.size()));
         if (e == cudaSuccess && st == PG_OK) e = cudaEventRecord(slot->done, slot->stream);
     }
     const double t = s->now();
@@ -942,6 +1042,7 @@ pg_status pg_permute_batch(uint64_t *states, size_t n, void *stream) {
     const uint64_t want = (n + 127) / 128;
     const uint64_t cap = (uint64_t)g.sms * g.permute_blocks_per_sm * 8;
     const unsigned grid = (unsigned)(want < cap ? want : cap);
+    ProfScope prof(kIdPermute, as_stream(stream), (uint64_t)n);
     if (g.params_set == 1) dev::k_permute<dev::kMdsSmall><<<grid, 128, 0, as_stream(stream)>>>(states, (uint64_t)n, vec16);
     else dev::k_permute<dev::kMdsFull><<<grid, 128, 0, as_stream(stream)>>>(states, (uint64_t)n, vec16);
     PG_CUDA(cudaGetLastError());
@@ -960,6 +1061,7 @@ pg_status pg_hash_rows(const uint64_t *rows, size_t n_rows, size_t width, uint64
     const uint64_t want = (n_rows + 127) / 128;
     const uint64_t cap = (uint64_t)g.sms * g.permute_blocks_per_sm * 8;
     const unsigned grid = (unsigned)(want < cap ? want : cap);
+    ProfScope prof(kIdHashRows, as_stream(stream), (uint64_t)n_rows * ((width + kRate - 1) / kRate));
     if (g.params_set == 1)
         dev::k_hash_rows<dev::kMdsSmall><<<grid, 128, 0, as_stream(stream)>>>(rows, (uint64_t)n_rows, (uint64_t)width, vec16, digests);
     else
@@ -1001,17 +1103,21 @@ pg_status pg_merkle_build(const uint64_t *rows, size_t n_leaves, size_t width, u
     if (small) {
         const uint64_t threads = (uint64_t)n_leaves * 16;
         const unsigned grid = (unsigned)((threads + dev::kTopBlock - 1) / dev::kTopBlock);
+        ProfScope prof(kIdMerkleTopLeaf, st, (uint64_t)n_leaves * ((width + kRate - 1) / kRate));
         dev::k_merkle_top_leaf<<<grid, dev::kTopBlock, 0, st>>>(rows, (uint64_t)n_leaves, (uint64_t)width, nodes);
         PG_CUDA(cudaGetLastError());
     } else {
         PG_CUDA(cudaMemcpyAsync(d_plan, &tp, sizeof tp, cudaMemcpyHostToDevice, st));
         PG_CUDA(cudaMemsetAsync(d_counters, 0, counter_bytes, st));
-        s = launch_merkle(nullptr, d_plan, 1u, tasks, d_counters, st);
+        // leaf sponges plus the nodes of levels 1 .. first_top-1
+        const uint64_t perms = tree_perms(n_leaves, width) - ((n_leaves >> (first_top - 1)) - 1);
+        s = launch_merkle(nullptr, d_plan, 1u, tasks, d_counters, st, perms);
         if (s != PG_OK) return s;
     }
     for (uint32_t l = first_top; l <= tp.log_n; ++l) {
         const uint64_t threads = (n_leaves >> l) * 16;
         const unsigned grid = (unsigned)((threads + dev::kTopBlock - 1) / dev::kTopBlock);
+        ProfScope prof(kIdMerkleTop, st, (uint64_t)n_leaves >> l);
         dev::k_merkle_top<<<grid, dev::kTopBlock, 0, st>>>(nodes, (uint64_t)n_leaves, l);
         PG_CUDA(cudaGetLastError());
     }
@@ -1040,7 +1146,7 @@ pg_status pg_merkle_build_batch(const pg_tree *trees, size_t n_trees, const pg_s
     auto *d_counters = reinterpret_cast<uint32_t *>(g.ws + kPlanBytes);
     PG_CUDA(cudaMemcpyAsync(d_plan, plans.data(), plan_bytes, cudaMemcpyHostToDevice, st));
     PG_CUDA(cudaMemsetAsync(d_counters, 0, counter_bytes, st));
-    return launch_merkle(sched, d_plan, (uint32_t)plans.size(), tasks, d_counters, st);
+    return launch_merkle(sched, d_plan, (uint32_t)plans.size(), tasks, d_counters, st, batch_perms(trees, n_trees));
 }
 
 pg_status pg_batch_graph_create(const pg_tree *trees, size_t n_trees, const pg_schedule *sched,
@@ -1063,6 +1169,7 @@ pg_status pg_batch_graph_create(const pg_tree *trees, size_t n_trees, const pg_s
     h->n_trees = (uint32_t)plans.size();
     h->tasks = tasks;
     h->counters = counters;
+    h->perms = batch_perms(trees, n_trees);
     const size_t plan_bytes_aligned = (h->plan_bytes + 255) & ~(size_t)255;
     const size_t total = plan_bytes_aligned + sizeof(uint32_t) * (1 + (size_t)counters);
     cudaError_t e = cudaMalloc(&h->dmem, total);
@@ -1087,7 +1194,7 @@ pg_status pg_batch_graph_create(const pg_tree *trees, size_t n_trees, const pg_s
     e = cudaStreamBeginCapture(h->capture, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cleanup(fail(PG_ERR_CUDA, "begin capture: %s", cudaGetErrorString(e)));
     cudaError_t e_memset = cudaMemsetAsync(d_counters, 0, sizeof(uint32_t) * (1 + (size_t)counters), h->capture);
-    pg_status sl = launch_merkle(&h->sched, d_plan, h->n_trees, tasks, d_counters, h->capture);
+    pg_status sl = launch_merkle(&h->sched, d_plan, h->n_trees, tasks, d_counters, h->capture, h->perms);
     e = cudaStreamEndCapture(h->capture, &h->graph);
     if (e_memset != cudaSuccess || sl != PG_OK || e != cudaSuccess)
         return cleanup(sl != PG_OK ? sl : fail(PG_ERR_CUDA, "capture: %s", cudaGetErrorString(e != cudaSuccess ? e : e_memset)));
@@ -1099,6 +1206,7 @@ pg_status pg_batch_graph_create(const pg_tree *trees, size_t n_trees, const pg_s
 
 pg_status pg_batch_graph_launch(pg_batch_graph *graph, void *stream) {
     if (!graph) return fail(PG_ERR_INVALID_ARG, "graph is NULL");
+    pg12::ProfScope prof(pg12::kIdGraph, as_stream(stream), graph->perms);
     PG_CUDA(cudaGraphLaunch(graph->exec, as_stream(stream)));
     return PG_OK;
 }
@@ -1314,6 +1422,7 @@ pg_status pg_merkle_open(const uint64_t *nodes, size_t n_leaves, const uint64_t 
     if (depth == 0) return PG_OK;  // a one-leaf tree has empty paths
     const uint64_t threads = (uint64_t)k * depth;
     const unsigned grid = (unsigned)((threads + 255) / 256);
+    pg12::ProfScope prof(pg12::kIdOpen, as_stream(stream), 0);
     dev::k_merkle_open<<<grid, 256, 0, as_stream(stream)>>>(nodes, (uint64_t)n_leaves, depth, indices, (uint64_t)k, paths);
     PG_CUDA(cudaGetLastError());
     return PG_OK;
@@ -1328,6 +1437,7 @@ pg_status pg_merkle_verify(const uint64_t *root, size_t n_leaves, const uint64_t
     if (!root || !leaves || !indices || !ok || (!paths && n_leaves > 1)) return fail(PG_ERR_INVALID_ARG, "NULL buffer");
     const uint32_t depth = log2u(n_leaves);
     const unsigned grid = (unsigned)((k + dev::kVerifyBlock - 1) / dev::kVerifyBlock);
+    ProfScope prof(kIdVerify, as_stream(stream), (uint64_t)k * depth);
     if (g.params_set == 1)
         dev::k_merkle_verify<dev::kMdsSmall><<<grid, dev::kVerifyBlock, 0, as_stream(stream)>>>(root, depth, (uint64_t)n_leaves,
                                                                                              leaves, indices, (uint64_t)k, paths, ok);
@@ -1396,9 +1506,72 @@ pg_status pg_merkle_build_noalloc(const uint64_t *rows, size_t n_leaves, size_t 
     const uint32_t want = (tasks + warps_per_block - 1) / warps_per_block;
     const uint32_t cap = (uint32_t)(sm_count[device] * blocks_per_sm[device]);
     const unsigned grid = want < cap ? want : cap;
+    ProfScope prof(kIdSingle, st, tree_perms(n_leaves, width));
     if (g.params_set == 1) dev::k_merkle_single<dev::kMdsSmall><<<grid, dev::kBlock, 0, st>>>(tp, tasks, scratch + 1, scratch);
     else dev::k_merkle_single<dev::kMdsFull><<<grid, dev::kBlock, 0, st>>>(tp, tasks, scratch + 1, scratch);
     PG_CUDA(cudaGetLastError());
+    return PG_OK;
+}
+
+pg_status pg_profile_enable(int on) {
+    std::vector<pg12::ProfRecord> old;
+    {
+        std::lock_guard<std::mutex> lk(pg12::g_prof.mu);
+        pg12::g_prof.on.store(on != 0);
+        old.swap(pg12::g_prof.recs);
+        pg12::g_prof.dropped = 0;
+    }
+    // events of discarded records go back to the spare list once they have completed
+    for (auto &r : old) cudaEventSynchronize(r.b);
+    std::lock_guard<std::mutex> lk(pg12::g_prof.mu);
+    for (auto &r : old) {
+        pg12::g_prof.spare.emplace_back(r.device, r.a);
+        pg12::g_prof.spare.emplace_back(r.device, r.b);
+    }
+    return PG_OK;
+}
+
+pg_status pg_profile_read(pg_kernel_time *out, size_t cap, size_t *n_out, uint64_t *dropped) {
+    std::vector<pg12::ProfRecord> recs;
+    uint64_t drop = 0;
+    {
+        std::lock_guard<std::mutex> lk(pg12::g_prof.mu);
+        recs.swap(pg12::g_prof.recs);
+        drop = pg12::g_prof.dropped;
+        pg12::g_prof.dropped = 0;
+    }
+    pg_kernel_time acc[pg12::kIdCount];
+    std::memset(acc, 0, sizeof acc);
+    cudaError_t err = cudaSuccess;
+    for (auto &r : recs) {
+        float ms = 0.f;
+        cudaError_t e = cudaEventSynchronize(r.b);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, r.a, r.b);
+        if (e != cudaSuccess && err == cudaSuccess) err = e;
+        acc[r.kid].launches += 1;
+        acc[r.kid].perms += r.perms;
+        acc[r.kid].total_ms += ms;
+    }
+    {
+        std::lock_guard<std::mutex> lk(pg12::g_prof.mu);
+        for (auto &r : recs) {
+            pg12::g_prof.spare.emplace_back(r.device, r.a);
+            pg12::g_prof.spare.emplace_back(r.device, r.b);
+        }
+    }
+    size_t n = 0;
+    for (int kid = 0; kid < pg12::kIdCount; ++kid) {
+        if (acc[kid].launches == 0) continue;
+        if (out && n < cap) {
+            out[n] = acc[kid];
+            std::snprintf(out[n].name, sizeof out[n].name, "%s", pg12::kKernelNames[kid]);
+        }
+        ++n;
+    }
+    if (n_out) *n_out = n;
+    if (dropped) *dropped = drop;
+    if (err != cudaSuccess) return fail(PG_ERR_CUDA, "profile events: %s", cudaGetErrorString(err));
+    if (out && n > cap) return fail(PG_ERR_INVALID_ARG, "profile has %zu kernels, cap is %zu", n, cap);
     return PG_OK;
 }
 

@@ -52,3 +52,12 @@ def test_device_calls_refuse_before_init(lib):
 
 def test_init_rejects_external_params(lib):
     assert pg.load().pg_init(0, b"/nonexistent") == 6
+
+
+def test_profile_store_empty_on_host(lib):
+    # with nothing recorded, enabling and reading the launch-timing store
+    # makes no CUDA call
+    pg.profile_enable(True)
+    got = pg.profile_read()
+    pg.profile_enable(False)
+    assert got == {"_dropped": 0}

@@ -1,0 +1,81 @@
+"""Launch timing (pg_profile_enable / pg_profile_read) on the GPU.
+
+The permutations the library attributes to its launches must add up to the
+work the method defines (Sec. 2.4: ceil(w/8) sponge permutations per leaf
+plus one per inner node), whichever kernels a build is split across.
+"""
+import numpy as np
+import pytest
+
+import pg_synth
+
+torch = pytest.importorskip("torch")
+pg = pytest.importorskip("paper_2506_09505_gb300")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def ready():
+    pg.load(build_if_missing=True)
+    pg.init(0)
+    yield
+    pg.profile_enable(False)
+
+
+def _rows(log_n, w, seed):
+    return pg_synth.matrix_torch(seed, 1 << log_n, w, device="cuda")
+
+
+def _tree_perms(n, w):
+    return n * ((w + 7) // 8) + n - 1
+
+
+@pytest.mark.parametrize("log_n,w", [(4, 8), (12, 3), (16, 8), (17, 20), (20, 8)])
+def test_build_launches_account_for_every_permutation(log_n, w):
+    rows = _rows(log_n, w, 0x7000 + log_n)
+    nodes = torch.empty((2 * (1 << log_n) - 1, 4), dtype=torch.int64, device="cuda")
+    pg.profile_enable(True)
+    pg.merkle_build(rows, nodes)
+    pg.merkle_build(rows, nodes)
+    got = pg.profile_read()
+    pg.profile_enable(False)
+    assert got.pop("_dropped") == 0
+    assert sum(v["perms"] for v in got.values()) == 2 * _tree_perms(1 << log_n, w)
+    assert all(v["total_ms"] > 0 for v in got.values())
+    if (1 << log_n) > 32768:
+        assert got["k_merkle"]["launches"] == 2
+    else:
+        assert "k_merkle" not in got and got["k_merkle_top_leaf"]["launches"] == 2
+    top_levels = sum(1 for l in range(1, log_n + 1) if (1 << log_n) >> l <= 32768)
+    assert got.get("k_merkle_top", {"launches": 0})["launches"] == 2 * top_levels
+
+
+def test_other_entry_points_are_recorded():
+    st = pg_synth.matrix_torch(0x7100, 1000, 12, device="cuda")
+    rows = _rows(10, 8, 0x7101)
+    pg.profile_enable(True)
+    pg.permute_batch(st)
+    pg.hash_rows(rows)
+    trees = [_rows(9, 8, 0x7102), _rows(11, 16, 0x7103)]
+    nodes = pg.alloc_nodes(trees)
+    pg.merkle_build_batch(trees, nodes)
+    g = pg.BatchGraph(trees, nodes)
+    g.launch()
+    got = pg.profile_read()
+    g.close()
+    pg.profile_enable(False)
+    assert got["k_permute"] == {"launches": 1, "perms": 1000, "total_ms": got["k_permute"]["total_ms"]}
+    assert got["k_hash_rows"]["perms"] == 1024
+    batch = _tree_perms(1 << 9, 8) + _tree_perms(1 << 11, 16)
+    # the batch launch and the graph launch (captured launches are not recorded)
+    assert got["k_merkle"]["launches"] == 1 and got["k_merkle"]["perms"] == batch
+    assert got["batch_graph"]["launches"] == 1 and got["batch_graph"]["perms"] == batch
+
+
+def test_disabled_records_nothing():
+    pg.profile_enable(False)
+    rows = _rows(8, 8, 0x7200)
+    pg.hash_rows(rows)
+    torch.cuda.synchronize()
+    assert pg.profile_read() == {"_dropped": 0}
