@@ -2,12 +2,14 @@
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package.  The product library never calls it and
-shares no code with it.  The arithmetic lives in ``pg_oracle.c`` (plain
-``unsigned __int128`` products followed by ``% p``); this module only loads
-that shared object with ctypes and marshals numpy arrays.
+shares no code with it.  The arithmetic lives in ``pg_oracle.c`` and
+``ntt_oracle.c`` (plain ``unsigned __int128`` products followed by ``% p``);
+this module only loads that shared object with ctypes and marshals numpy
+arrays.
 
 Functions follow arXiv 2506.09505: Eq. 1 (the field), Alg. 1 and Sec. 2.4
-(the permutation and the sponge), Sec. 2.4 / Sec. 4.2 (the Merkle tree).
+(the permutation and the sponge), Sec. 2.4 / Sec. 4.2 (the Merkle tree), and
+the textbook NTT / low-degree extension behind the Sec. 2.3 NTT hotspot.
 """
 from __future__ import annotations
 
@@ -22,7 +24,7 @@ T = 12
 ROUNDS = 30
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "pg_oracle.c")
+_SRCS = [os.path.join(_HERE, "pg_oracle.c"), os.path.join(_HERE, "ntt_oracle.c")]
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
@@ -30,11 +32,11 @@ _u64p = ctypes.POINTER(ctypes.c_uint64)
 
 
 def build(force: bool = False) -> str:
-    """Compile pg_oracle.c into liboracle.so (plain gcc, -O2, pthreads)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    """Compile the oracle's C sources into liboracle.so (plain gcc, -O2, pthreads)."""
+    if force or not os.path.exists(_LIB) or any(os.path.getmtime(_LIB) < os.path.getmtime(s) for s in _SRCS):
         tmp = _LIB + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-pthread",
-                               _SRC, "-o", tmp])
+                               *_SRCS, "-o", tmp])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -68,6 +70,13 @@ def _load():
         "orc_count_singular_minors": (ctypes.c_long, [_u64p, ctypes.POINTER(ctypes.c_long)]),
         "orc_is_mds": (i, [_u64p]),
         "orc_params_generate_small": (i, [_u64p, _u64p, _u64p]),
+        "orc_two_adic_root": (u64, [i, i]),
+        "orc_dft_naive": (i, [_u64p, _u64p, sz, i]),
+        "orc_fft": (i, [_u64p, sz, i]),
+        "orc_ntt_columns": (i, [_u64p, sz, sz, i]),
+        "orc_poly_eval": (u64, [_u64p, sz, u64]),
+        "orc_interpolate_columns": (i, [_u64p, sz, sz, _u64p]),
+        "orc_lde_columns": (i, [_u64p, sz, sz, i, u64, _u64p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -282,3 +291,64 @@ def level_offsets(n_leaves: int):
         base += cnt
         cnt //= 2
     return offs
+
+
+# ------------------------------------------------------ NTT / LDE (Sec. 2.3)
+GENERATOR = 7      # generates the multiplicative group of Eq. 1's field
+LDE_SHIFT = 7      # coset shift of the low-degree extension
+
+
+def two_adic_root(log_n: int, inverse: bool = False) -> int:
+    """Primitive 2^log_n-th root of unity 7^((p-1)/2^log_n) (or its inverse)."""
+    return int(_load().orc_two_adic_root(log_n, 1 if inverse else 0))
+
+
+def dft_naive(x, inverse: bool = False) -> np.ndarray:
+    """The definition: y_i = sum_j x_j w^(ij) (inverse: w^-1, times n^-1)."""
+    x = _u64(x)
+    y = np.zeros_like(x)
+    if _load().orc_dft_naive(_ptr(x), _ptr(y), x.size, 1 if inverse else 0) != 0:
+        raise ValueError("length must be a power of two")
+    return y
+
+
+def fft(x, inverse: bool = False) -> np.ndarray:
+    """Recursive radix-2 evaluation of the same transform."""
+    y = _u64(x).copy()
+    if _load().orc_fft(_ptr(y), y.size, 1 if inverse else 0) != 0:
+        raise ValueError("length must be a power of two")
+    return y
+
+
+def ntt_columns(data, inverse: bool = False) -> np.ndarray:
+    """Transform every column of a row-major (n, ncols) array."""
+    d = _u64(data).copy()
+    n, c = d.shape
+    if _load().orc_ntt_columns(_ptr(d), n, c, 1 if inverse else 0) != 0:
+        raise ValueError("row count must be a power of two")
+    return d
+
+
+def poly_eval(coeffs, x: int) -> int:
+    """Horner: sum_j c_j x^j."""
+    c = _u64(coeffs)
+    return int(_load().orc_poly_eval(_ptr(c), c.size, x))
+
+
+def interpolate_columns(evals) -> np.ndarray:
+    """Coefficients (rows = powers) of every column's interpolant on the subgroup."""
+    e = _u64(evals)
+    out = np.zeros_like(e)
+    if _load().orc_interpolate_columns(_ptr(e), e.shape[0], e.shape[1], _ptr(out)) != 0:
+        raise ValueError("row count must be a power of two")
+    return out
+
+
+def lde_columns(evals, log_blowup: int, shift: int = LDE_SHIFT) -> np.ndarray:
+    """(n 2^b, ncols): column c at row i is P_c(shift * w^i), w of order n 2^b."""
+    e = _u64(evals)
+    n, c = e.shape
+    out = np.zeros((n << log_blowup, c), dtype=np.uint64)
+    if _load().orc_lde_columns(_ptr(e), n, c, log_blowup, shift, _ptr(out)) != 0:
+        raise ValueError("bad LDE arguments")
+    return out
