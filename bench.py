@@ -54,10 +54,13 @@ def parse_args():
     ap.add_argument("--width", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--workload", choices=["merkle", "permute", "batch", "serve"], default="merkle",
+    ap.add_argument("--workload", choices=["merkle", "permute", "batch", "serve", "lde"], default="merkle",
                     help="merkle (default): one 2^log_n-leaf tree per step; permute: 2^24 raw "
                          "permutations; batch: 64 mixed trees, one graph launch vs one launch per "
-                         "tree; serve: Poisson stream of tree-build requests")
+                         "tree; serve: Poisson stream of tree-build requests; lde: low-degree "
+                         "extension of a trace, then its Merkle commitment")
+    ap.add_argument("--lde-log-n", type=int, default=21)
+    ap.add_argument("--log-blowup", type=int, default=1)
     ap.add_argument("--trees", type=int, default=64)
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--rate", type=float, default=200.0)
@@ -543,6 +546,57 @@ def run_serve(args):
     return 0
 
 
+def run_lde(args):
+    """Low-degree extension of a 2^21-row, 8-column trace with blowup 2 (the NTT
+    hotspot), committed as the 2^22 x 8 Merkle tree, every step."""
+    torch, pg = _device_setup()
+    import pg_synth
+    log_n, cols, log_b = args.lde_log_n, args.width, args.log_blowup
+    n, big = 1 << log_n, 1 << (log_n + log_b)
+    evals = pg_synth.matrix_torch(pg_synth.config_seed(6), n, cols, device="cuda")
+    scratch = torch.empty_like(evals)
+    out = torch.empty((big, cols), dtype=torch.int64, device="cuda")
+    nodes = torch.empty((2 * big - 1, 4), dtype=torch.int64, device="cuda")
+    for _ in range(args.warmup):
+        pg.lde(evals, log_b, out=out, scratch=scratch)
+        pg.merkle_build(out, nodes)
+    torch.cuda.synchronize()
+    pg.profile_enable(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        pg.lde(evals, log_b, out=out, scratch=scratch)
+        pg.merkle_build(out, nodes)
+    e1.record()
+    torch.cuda.synchronize()
+    kern = pg.profile_read()
+    pg.profile_enable(False)
+    kern.pop("_dropped", None)
+    ms = e0.elapsed_time(e1) / args.steps
+    lde_ms = kern["k_ntt_pass"]["total_ms"] / args.steps
+    # one product per butterfly (8 results) and three per coefficient for the coset factor
+    butterflies = (n // 2) * log_n * cols + (big // 2) * log_n * cols
+    mul_results = 8 * (butterflies + 4 * n * cols)
+    alg_bytes = 8 * cols * (n + big)
+    perms = big * ((cols + 7) // 8) + big - 1
+    peaks = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    print(json.dumps({
+        "workload": f"LDE of 2^{log_n} x {cols} evaluations, blowup 2^{log_b}, then the 2^{log_n + log_b} x {cols} Merkle tree",
+        "ms_per_step": ms, "steps": args.steps,
+        "lde": {"ms": lde_ms, "launches_per_step": kern["k_ntt_pass"]["launches"] // args.steps,
+                "roofline_alu": {"achieved": mul_results / (lde_ms / 1e3) / 1e12, "peak": _peak_results_per_s() / 1e12,
+                                 "unit": "T mul32-results/s",
+                                 "frac": mul_results / (lde_ms / 1e3) / _peak_results_per_s()},
+                "roofline_hbm": {"achieved": alg_bytes / (lde_ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                                 "frac": alg_bytes / (lde_ms / 1e3) / 1e9 / hbm,
+                                 "algorithmic_bytes": alg_bytes}},
+        "commit": {"ms": ms - lde_ms, "perms": perms, "perms_per_s": perms / ((ms - lde_ms) / 1e3)},
+        "kernels": {k: {"launches": v["launches"], "ms_per_step": v["total_ms"] / args.steps} for k, v in kern.items()},
+    }), flush=True)
+    return 0
+
+
 def main():
     global _ARGS
     args = parse_args()
@@ -555,6 +609,8 @@ def main():
         return run_batch(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "lde":
+        return run_lde(args)
     return run_ours(args)
 
 

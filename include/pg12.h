@@ -346,6 +346,43 @@ pg_status pg_merkle_build_noalloc(const uint64_t *rows, size_t n_leaves, size_t 
                                   void *stream);
 
 /*
+ * Goldilocks NTT and low-degree extension (Sec. 2.3 names the NTT as
+ * zkProver's Goldilocks hotspot after Merkle building; Sec. 2.4 commits to
+ * polynomial evaluations).  The paper gives no definition; these are the
+ * textbook ones: 7 generates the multiplicative group of Eq. 1's field, the
+ * primitive 2^k-th root of unity is w_k = 7^((p - 1) / 2^k).
+ * Data is row-major with `ncols` columns: element (row r, column c) at
+ * r * ncols + c; every column is transformed on its own.  Inputs may hold
+ * any 64-bit words (read mod p); outputs are canonical.
+ *
+ * pg_ntt -- in place: X_i = sum_j x_j w^(i j) with w = w_k, n = 2^k rows;
+ * with inverse != 0, x_j = n^-1 sum_i X_i w^(-i j).  Natural row order in
+ * and out.
+ *   data   dev, n * ncols words, caller-owned, 8-byte aligned.
+ *   n      power of two, at most 2^30 (PG_ERR_NOT_POW2 / PG_ERR_INVALID_ARG).
+ * Needs pg_init().  Asynchronous on `stream`.
+ */
+pg_status pg_ntt(uint64_t *data, size_t n, size_t ncols, int inverse, void *stream);
+
+/*
+ * pg_lde -- low-degree extension with blowup 2^log_blowup on the coset
+ * shifted by 7: column c of `evals` holds P_c(w_k^j), j < n = 2^k, for the
+ * unique P_c of degree < n; row i of `out` receives P_c(7 * w_{k+b}^i),
+ * i < N = n * 2^b.  The rows of `out` are the leaves a Merkle commitment
+ * hashes (pg_merkle_build with width = ncols).
+ *   evals    dev, n * ncols words (read only unless it is also `scratch`).
+ *   out      dev, N * ncols words; must not overlap evals or scratch.
+ *   scratch  dev, n * ncols words of working space; may be `evals` itself
+ *            (then evals is overwritten).  On return it holds c_j 7^j (the
+ *            coefficients of P_c(7 x)) in bit-reversed row order.
+ *   log_blowup  0..16; N at most 2^30 rows.
+ * Needs pg_init().  Asynchronous on `stream`; PG_ERR_INVALID_ARG on bad
+ * sizes or overlapping buffers, PG_ERR_NOT_POW2 if n is not a power of two.
+ */
+pg_status pg_lde(const uint64_t *evals, size_t n, size_t ncols, uint32_t log_blowup, uint64_t *out,
+                 uint64_t *scratch, void *stream);
+
+/*
  * Launch timing (the cudaEvent side of the paper's hardware-counter
  * measurements, Sec. 4.1-4.2): when enabled, every kernel launch the library
  * makes (and every pg_batch_graph_launch) is bracketed by a pair of CUDA

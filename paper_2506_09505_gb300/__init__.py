@@ -113,6 +113,9 @@ SIGNATURES = {
                                      ctypes.c_size_t, ctypes.c_void_p]),
     "pg_field_bench": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                       ctypes.POINTER(ctypes.c_double)]),
+    "pg_ntt": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p]),
+    "pg_lde": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_size_t, ctypes.c_uint32,
+                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "pg_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "pg_profile_read": (ctypes.c_int, [ctypes.POINTER(KernelTime), ctypes.c_size_t,
                                        ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_uint64)]),
@@ -383,6 +386,32 @@ def field_bench(op: str):
     rate, per_clk = ctypes.c_double(), ctypes.c_double()
     _check(load().pg_field_bench(OPS[op], ctypes.byref(rate), ctypes.byref(per_clk)))
     return rate.value, per_clk.value
+
+
+def ntt(data, inverse: bool = False, stream=None):
+    """In-place NTT (or inverse) of every column of a (n, ncols) CUDA tensor."""
+    if data.dim() != 2:
+        raise ValueError("data must have shape (n, ncols)")
+    _check(load().pg_ntt(_dev_ptr(data, "data"), data.shape[0], data.shape[1], 1 if inverse else 0,
+                         _stream(stream)))
+    return data
+
+
+def lde(evals, log_blowup: int, out=None, scratch=None, stream=None):
+    """Low-degree extension of the (n, ncols) CUDA tensor ``evals`` onto the
+    coset 7 * <w_N>, N = n * 2^log_blowup -> (N, ncols).  ``scratch`` (n, ncols)
+    is allocated when not given; pass ``evals`` to work in place."""
+    import torch
+    if evals.dim() != 2:
+        raise ValueError("evals must have shape (n, ncols)")
+    n, c = evals.shape
+    if out is None:
+        out = torch.empty((n << log_blowup, c), dtype=evals.dtype, device=evals.device)
+    if scratch is None:
+        scratch = torch.empty_like(evals)
+    _check(load().pg_lde(_dev_ptr(evals, "evals"), n, c, log_blowup, _dev_ptr(out, "out"),
+                         _dev_ptr(scratch, "scratch"), _stream(stream)))
+    return out
 
 
 def profile_enable(on: bool = True) -> None:

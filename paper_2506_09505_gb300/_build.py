@@ -1,9 +1,12 @@
 """Build of the in-tree CUDA library ``libpg12.so`` (sm_103a only).
 
-Two translation units compiled in parallel with nvcc and linked into one
+Four translation units compiled in parallel with nvcc and linked into one
 shared object next to this file:
-  csrc/params.cpp  host: parameter set pg12_v1 and the sparse rewrite
-  csrc/pg12.cu     device kernels and the C ABI declared in include/pg12.h
+  csrc/params.cpp  host: parameter sets pg12_v1 / pg12_small and the sparse rewrite
+  csrc/pg12.cu     permutation, sponge and Merkle kernels, serving runtime, most of
+                   the C ABI declared in include/pg12.h
+  csrc/ops.cu      element-wise field operations and their microbenchmarks
+  csrc/ntt.cu      NTT and low-degree extension
 """
 from __future__ import annotations
 
@@ -24,7 +27,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 # extra nvcc flags for tuning builds, e.g. PG12_NVCC_FLAGS="-DPG12_MERKLE_MIN_BLOCKS=4"
 EXTRA = os.environ.get("PG12_NVCC_FLAGS", "").split()
-SOURCES = ["params.cpp", "pg12.cu", "ops.cu"]
+SOURCES = ["params.cpp", "pg12.cu", "ops.cu", "ntt.cu"]
 
 
 def nvcc() -> str:

@@ -465,13 +465,10 @@ constexpr size_t kPlanBytes = 4u << 20;        // first part: plans; rest: count
 // CUDA events is recorded on the launching stream around each launch and
 // resolved when the records are read.  Launches inside a stream capture are
 // not recorded (the graph launch is, as one entry).
-enum KernelId {
-    kIdMerkle, kIdMerkleTop, kIdMerkleTopLeaf, kIdPermute, kIdHashRows, kIdOpen, kIdVerify, kIdSingle,
-    kIdGraph, kIdCount
-};
 const char *const kKernelNames[kIdCount] = {"k_merkle",      "k_merkle_top",    "k_merkle_top_leaf",
                                             "k_permute",     "k_hash_rows",     "k_merkle_open",
-                                            "k_merkle_verify", "k_merkle_single", "batch_graph"};
+                                            "k_merkle_verify", "k_merkle_single", "batch_graph",
+                                            "k_ntt_pass",    "k_ntt_bitrev"};
 constexpr size_t kProfMaxRecords = 1u << 16;
 
 struct ProfRecord {
@@ -501,50 +498,6 @@ struct Profiler {
     }
 };
 Profiler g_prof;
-
-// Records one launch (the kernel launched between construction and
-// destruction) when profiling is on.
-class ProfScope {
-  public:
-    ProfScope(int kid, cudaStream_t st, uint64_t perms) : st_(st) {
-        if (!g_prof.on.load(std::memory_order_relaxed)) return;
-        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-        if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
-        int device = 0;
-        if (cudaGetDevice(&device) != cudaSuccess) return;
-        std::lock_guard<std::mutex> lk(g_prof.mu);
-        if (g_prof.recs.size() >= kProfMaxRecords) {
-            ++g_prof.dropped;
-            return;
-        }
-        rec_ = ProfRecord{kid, device, perms, g_prof.take(device), nullptr};
-        if (rec_.a) rec_.b = g_prof.take(device);
-        if (!rec_.a || !rec_.b || cudaEventRecord(rec_.a, st) != cudaSuccess) {
-            if (rec_.a) g_prof.spare.emplace_back(device, rec_.a);
-            if (rec_.b) g_prof.spare.emplace_back(device, rec_.b);
-            return;
-        }
-        active_ = true;
-    }
-    ~ProfScope() {
-        if (!active_) return;
-        const bool ok = cudaEventRecord(rec_.b, st_) == cudaSuccess;
-        std::lock_guard<std::mutex> lk(g_prof.mu);
-        if (ok) {
-            g_prof.recs.push_back(rec_);
-        } else {
-            g_prof.spare.emplace_back(rec_.device, rec_.a);
-            g_prof.spare.emplace_back(rec_.device, rec_.b);
-        }
-    }
-    ProfScope(const ProfScope &) = delete;
-    ProfScope &operator=(const ProfScope &) = delete;
-
-  private:
-    cudaStream_t st_;
-    ProfRecord rec_{};
-    bool active_ = false;
-};
 
 // Permutations of a whole tree: ceil(w/8) per leaf plus one per inner node.
 uint64_t tree_perms(uint64_t n, uint64_t w) { return n * ((w + kRate - 1) / kRate) + (n - 1); }
@@ -677,6 +630,48 @@ pg_status launch_merkle(const pg_schedule *sched, const dev::TreePlan *d_plans, 
 }
 
 }  // namespace
+
+int ntt_require_init() {
+    std::lock_guard<std::mutex> lk(g_mu);
+    return g.init ? (int)PG_OK : fail(PG_ERR_NOT_INIT, "pg_init() has not been called");
+}
+
+ProfScope::ProfScope(int kid, void *stream, uint64_t perms) : st_(stream), kid_(kid), perms_(perms) {
+    if (!g_prof.on.load(std::memory_order_relaxed)) return;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
+    if (cudaGetDevice(&device_) != cudaSuccess) return;
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    if (g_prof.recs.size() >= kProfMaxRecords) {
+        ++g_prof.dropped;
+        return;
+    }
+    cudaEvent_t a = g_prof.take(device_);
+    cudaEvent_t b = a ? g_prof.take(device_) : nullptr;
+    if (!a || !b || cudaEventRecord(a, st) != cudaSuccess) {
+        if (a) g_prof.spare.emplace_back(device_, a);
+        if (b) g_prof.spare.emplace_back(device_, b);
+        return;
+    }
+    a_ = a;
+    b_ = b;
+    active_ = true;
+}
+
+ProfScope::~ProfScope() {
+    if (!active_) return;
+    cudaEvent_t a = static_cast<cudaEvent_t>(a_), b = static_cast<cudaEvent_t>(b_);
+    const bool ok = cudaEventRecord(b, static_cast<cudaStream_t>(st_)) == cudaSuccess;
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    if (ok) {
+        g_prof.recs.push_back(ProfRecord{kid_, device_, perms_, a, b});
+    } else {
+        g_prof.spare.emplace_back(device_, a);
+        g_prof.spare.emplace_back(device_, b);
+    }
+}
+
 }  // namespace pg12
 
 struct pg_batch_graph {
@@ -995,6 +990,10 @@ pg_status pg_init(int device, const char *params_path) {
         dev::make_dev_consts(g.opt, dc);
         PG_CUDA(cudaMemcpyToSymbol(dev::c_dev, &dc, sizeof(dc)));
         PG_CUDA(cudaMemcpyToSymbol(dev::g_dev, &dc, sizeof(dc)));
+    }
+    {
+        const int ns = ntt_upload_constants();
+        if (ns != PG_OK) return (pg_status)ns;
     }
     PG_CUDA(cudaDeviceGetAttribute(&g.sms, cudaDevAttrMultiProcessorCount, device));
     {

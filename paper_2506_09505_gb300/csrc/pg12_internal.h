@@ -35,6 +35,35 @@ struct OptParams {
 // Records the text returned by pg_last_error() and passes `status` through.
 int set_error(int status, const char *fmt, ...);
 
+// Launch timing (pg_profile_enable / pg_profile_read): a ProfScope around a
+// launch records CUDA events on `stream` before and after it while timing is
+// on.  Defined in pg12.cu; the stream and events are held as opaque pointers.
+enum KernelId {
+    kIdMerkle, kIdMerkleTop, kIdMerkleTopLeaf, kIdPermute, kIdHashRows, kIdOpen, kIdVerify, kIdSingle,
+    kIdGraph, kIdNttPass, kIdNttBitrev, kIdCount
+};
+
+class ProfScope {
+  public:
+    ProfScope(int kid, void *stream, uint64_t perms);
+    ~ProfScope();
+    ProfScope(const ProfScope &) = delete;
+    ProfScope &operator=(const ProfScope &) = delete;
+
+  private:
+    void *st_ = nullptr;
+    void *a_ = nullptr, *b_ = nullptr;
+    int kid_ = 0, device_ = 0;
+    uint64_t perms_ = 0;
+    bool active_ = false;
+};
+
+// Uploads the NTT root and coset tables to the current device (ntt.cu);
+// pg_init calls it.
+int ntt_upload_constants();
+// PG_OK once pg_init has succeeded, else PG_ERR_NOT_INIT (pg12.cu).
+int ntt_require_init();
+
 namespace host {
 uint64_t fp_add(uint64_t a, uint64_t b);
 uint64_t fp_sub(uint64_t a, uint64_t b);
