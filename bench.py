@@ -41,7 +41,7 @@ IMAD_RESULTS_PER_CLK_SM = 64  # 32-bit multiply results per clock per SM
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_merkle
 # launch, from one ncu capture of the current kernel on that workload
 # (params, log2 leaves, width); other workloads report null.
-K_MERKLE_TRAFFIC = {("pg12_v1", 22, 8): 274_836_992 + 224_612_096}
+K_MERKLE_TRAFFIC = {("pg12_v1", 22, 8): 273_648_128 + 224_156_928}
 
 
 def parse_args():
