@@ -157,6 +157,24 @@ pg_status pg_shutdown(void);
 pg_status pg_params_export(uint64_t *rc, uint64_t *mds);
 
 /*
+ * pg_params_sha256 -- fingerprint of the active plain parameter set: the
+ * SHA-256 (FIPS 180-4) of rc[30][12] followed by mds[12][12], each word as
+ * 8 little-endian bytes, as 64 lowercase hex digits.  The returned string is
+ * owned by the library and stays valid until the process exits.  NULL if the
+ * set could not be generated.  Host-only; works without a GPU.
+ */
+const char *pg_params_sha256(void);
+
+/*
+ * pg_workspace_bytes -- device bytes of the library workspace that a batch of
+ * these trees needs (tree plans and arrival counters of pg_merkle_build_batch;
+ * the batch fails with PG_ERR_OOM above the workspace pg_init allocates).
+ * With trees == NULL: the size of that workspace.  0 if a tree's n_leaves is
+ * not a power of two.  Host-only.
+ */
+size_t pg_workspace_bytes(const pg_tree *trees, size_t n_trees);
+
+/*
  * pg_params_export_optimized -- host copy of the optimised-form constants
  * that the kernels use (Alg. 1's C, M, S after the sparse rewrite):
  *   full_rc   8*12 words: constants added before the S-box of full rounds

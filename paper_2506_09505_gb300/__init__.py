@@ -113,6 +113,8 @@ SIGNATURES = {
                                      ctypes.c_size_t, ctypes.c_void_p]),
     "pg_field_bench": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                       ctypes.POINTER(ctypes.c_double)]),
+    "pg_params_sha256": (ctypes.c_char_p, []),
+    "pg_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(Tree), ctypes.c_size_t]),
     "pg_ntt": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p]),
     "pg_lde": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_size_t, ctypes.c_uint32,
                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
@@ -412,6 +414,22 @@ def lde(evals, log_blowup: int, out=None, scratch=None, stream=None):
     _check(load().pg_lde(_dev_ptr(evals, "evals"), n, c, log_blowup, _dev_ptr(out, "out"),
                          _dev_ptr(scratch, "scratch"), _stream(stream)))
     return out
+
+
+def params_sha256() -> str:
+    """SHA-256 (hex) of the active plain parameter set: rc[30][12] then mds[12][12], little-endian words."""
+    h = load().pg_params_sha256()
+    if not h:
+        raise RuntimeError(last_error())
+    return h.decode()
+
+
+def workspace_bytes(rows_list=None, nodes_list=None) -> int:
+    """Workspace bytes a batch of trees needs (None: the size pg_init allocates)."""
+    if rows_list is None:
+        return int(load().pg_workspace_bytes(None, 0))
+    arr = _trees(rows_list, nodes_list if nodes_list is not None else alloc_nodes(rows_list))
+    return int(load().pg_workspace_bytes(arr, len(rows_list)))
 
 
 def profile_enable(on: bool = True) -> None:

@@ -287,5 +287,103 @@ bool derive_optimized(const PlainParams &pp, OptParams &op) {
     return true;
 }
 
+// ------------------------------------------------------------ SHA-256
+// FIPS 180-4 SHA-256 of a byte string, used to fingerprint a parameter set.
+// Its constants are computed from their definition rather than tabulated:
+// the initial hash words are the first 32 fractional bits of the square
+// roots of the first 8 primes, the round constants those of the cube roots
+// of the first 64 primes (integer roots of p * 2^64 and p * 2^96).
+namespace {
+
+typedef unsigned __int128 u128;
+
+// Both roots below are under 2^36 (primes up to 311, scaled by 2^64 / 2^96),
+// so the searches run over [0, 2^40], where mid^3 cannot overflow.
+uint64_t isqrt128(u128 v) {  // floor(sqrt(v)) for v < 2^80
+    uint64_t lo = 0, hi = 1ull << 40;
+    while (lo < hi) {
+        const uint64_t mid = lo + (hi - lo + 1) / 2;
+        if ((u128)mid * mid <= v) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+uint64_t icbrt128(u128 v) {  // floor(cbrt(v)) for v < 2^120
+    uint64_t lo = 0, hi = 1ull << 40;
+    while (lo < hi) {
+        const uint64_t mid = lo + (hi - lo + 1) / 2;
+        if ((u128)mid * mid * mid <= v) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+struct ShaConsts {
+    uint32_t h0[8], k[64];
+    ShaConsts() {
+        int found = 0;
+        for (uint32_t n = 2; found < 64; ++n) {
+            bool prime = true;
+            for (uint32_t d = 2; d * d <= n; ++d)
+                if (n % d == 0) prime = false;
+            if (!prime) continue;
+            if (found < 8) h0[found] = (uint32_t)isqrt128((u128)n << 64);
+            k[found] = (uint32_t)icbrt128((u128)n << 96);
+            ++found;
+        }
+    }
+};
+
+inline uint32_t rotr(uint32_t x, int r) { return (x >> r) | (x << (32 - r)); }
+
+void sha_block(uint32_t h[8], const uint8_t *blk, const ShaConsts &c) {
+    uint32_t w[64];
+    for (int i = 0; i < 16; ++i)
+        w[i] = ((uint32_t)blk[4 * i] << 24) | ((uint32_t)blk[4 * i + 1] << 16) | ((uint32_t)blk[4 * i + 2] << 8) |
+               (uint32_t)blk[4 * i + 3];
+    for (int i = 16; i < 64; ++i) {
+        const uint32_t s0 = rotr(w[i - 15], 7) ^ rotr(w[i - 15], 18) ^ (w[i - 15] >> 3);
+        const uint32_t s1 = rotr(w[i - 2], 17) ^ rotr(w[i - 2], 19) ^ (w[i - 2] >> 10);
+        w[i] = w[i - 16] + s0 + w[i - 7] + s1;
+    }
+    uint32_t a = h[0], b = h[1], cc = h[2], d = h[3], e = h[4], f = h[5], g = h[6], hh = h[7];
+    for (int i = 0; i < 64; ++i) {
+        const uint32_t t1 = hh + (rotr(e, 6) ^ rotr(e, 11) ^ rotr(e, 25)) + ((e & f) ^ (~e & g)) + c.k[i] + w[i];
+        const uint32_t t2 = (rotr(a, 2) ^ rotr(a, 13) ^ rotr(a, 22)) + ((a & b) ^ (a & cc) ^ (b & cc));
+        hh = g;
+        g = f;
+        f = e;
+        e = d + t1;
+        d = cc;
+        cc = b;
+        b = a;
+        a = t1 + t2;
+    }
+    h[0] += a; h[1] += b; h[2] += cc; h[3] += d; h[4] += e; h[5] += f; h[6] += g; h[7] += hh;
+}
+
+}  // namespace
+
+void sha256_hex(const uint8_t *data, size_t len, char out[65]) {
+    static const ShaConsts c;
+    uint32_t h[8];
+    std::memcpy(h, c.h0, sizeof h);
+    size_t off = 0;
+    for (; off + 64 <= len; off += 64) sha_block(h, data + off, c);
+    uint8_t tail[128] = {0};
+    const size_t rem = len - off;
+    std::memcpy(tail, data + off, rem);
+    tail[rem] = 0x80;
+    const size_t tlen = rem + 9 <= 64 ? 64 : 128;
+    const uint64_t bits = (uint64_t)len * 8;
+    for (int i = 0; i < 8; ++i) tail[tlen - 1 - i] = (uint8_t)(bits >> (8 * i));
+    for (size_t o = 0; o < tlen; o += 64) sha_block(h, tail + o, c);
+    static const char hex[] = "0123456789abcdef";
+    for (int i = 0; i < 8; ++i)
+        for (int j = 0; j < 8; ++j) out[8 * i + j] = hex[(h[i] >> (28 - 4 * j)) & 15];
+    out[64] = 0;
+}
+
 }  // namespace host
 }  // namespace pg12

@@ -933,6 +933,39 @@ pg_status pg_params_export(uint64_t *rc, uint64_t *mds) {
     return PG_OK;
 }
 
+const char *pg_params_sha256(void) {
+    static char hex[2][65];
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (ensure_params() != PG_OK) return nullptr;
+    // rc[30][12] then mds[12][12], little-endian words
+    uint8_t buf[sizeof g.plain.rc + sizeof g.plain.mds];
+    size_t o = 0;
+    auto put = [&](uint64_t w) {
+        for (int b = 0; b < 8; ++b) buf[o++] = (uint8_t)(w >> (8 * b));
+    };
+    for (int r = 0; r < kRounds; ++r)
+        for (int i = 0; i < kT; ++i) put(g.plain.rc[r][i]);
+    for (int i = 0; i < kT; ++i)
+        for (int j = 0; j < kT; ++j) put(g.plain.mds[i][j]);
+    char *out = hex[g.params_set == 1 ? 1 : 0];
+    host::sha256_hex(buf, o, out);
+    return out;
+}
+
+size_t pg_workspace_bytes(const pg_tree *trees, size_t n_trees) {
+    if (!trees) return kWorkspaceBytes;
+    uint64_t counters = 0;
+    for (size_t k = 0; k < n_trees; ++k) {
+        if (!is_pow2(trees[k].n_leaves)) return 0;
+        dev::TreePlan tp;
+        std::memset(&tp, 0, sizeof tp);
+        uint32_t nc = 0;
+        plan_tree(tp, trees[k].rows, trees[k].n_leaves, trees[k].width ? trees[k].width : 1, trees[k].nodes, 0, 0, nc);
+        counters += nc;
+    }
+    return kPlanBytes + sizeof(uint32_t) * (1 + (size_t)counters);
+}
+
 pg_status pg_params_export_optimized(uint64_t *full_rc, uint64_t *mds, uint64_t *pre, uint64_t *part_rc,
                                      uint64_t *part_v, uint64_t *part_w) {
     std::lock_guard<std::mutex> lk(g_mu);

@@ -76,6 +76,8 @@ void generate_plain(PlainParams &pp);
 // candidate's index.
 int generate_small(PlainParams &pp, uint32_t row[kT]);
 bool derive_optimized(const PlainParams &pp, OptParams &op);
+// FIPS 180-4 SHA-256 of `len` bytes as 64 lowercase hex digits.
+void sha256_hex(const uint8_t *data, size_t len, char out[65]);
 }  // namespace host
 
 }  // namespace pg12

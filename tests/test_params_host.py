@@ -7,6 +7,8 @@ evaluated with Python integers (round structure of Alg. 1: MDSPartial with
 vec[0] = first row, vec[1] = first column) against the oracle's plain
 permutation.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -93,3 +95,49 @@ def test_unknown_set_rejected(lib):
     with pytest.raises(pg.PGError) as e:
         pg.params_select("nope")
     assert e.value.status == 6
+
+
+def _golden_sha():
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "pg12_v1.sha256")
+    with open(path) as f:
+        return dict(line.split() for line in f if line.strip())["sha256"]
+
+
+def test_library_sha256_matches_golden_and_hashlib():
+    import hashlib
+    lib = pytest.importorskip("paper_2506_09505_gb300")
+    lib.load(build_if_missing=True)
+    lib.params_select(None)
+    assert lib.params_sha256() == _golden_sha()
+    for name in ("pg12_small", None):
+        lib.params_select(name)
+        rc, mds = lib.params_export()
+        h = hashlib.sha256(np.ascontiguousarray(rc, dtype="<u8").tobytes() +
+                           np.ascontiguousarray(mds, dtype="<u8").tobytes()).hexdigest()
+        assert lib.params_sha256() == h
+    assert lib.params_sha256() == _golden_sha()
+
+
+def test_workspace_bytes_counts_plans_and_counters():
+    import ctypes
+    lib = pytest.importorskip("paper_2506_09505_gb300")
+    raw = lib.load(build_if_missing=True)
+    total = raw.pg_workspace_bytes(None, 0)
+    assert total == 32 << 20
+    sizes = [(1, 8), (32, 8), (64, 3), (1 << 12, 16), (1 << 20, 8)]
+    arr = (lib.Tree * len(sizes))()
+    for k, (n, w) in enumerate(sizes):
+        arr[k].rows, arr[k].n_leaves, arr[k].width, arr[k].nodes = 0x1000, n, w, 0x2000
+
+    def counters(n):
+        # one arrival counter per 32-node group of each level whose children span more than one group
+        c, lvl = 0, 1
+        while (n >> lvl) >= 1 and lvl <= n.bit_length() - 1:
+            if (n >> (lvl - 1)) > 32:
+                c += ((n >> lvl) + 31) // 32
+            lvl += 1
+        return c
+    want = (4 << 20) + 4 * (1 + sum(counters(n) for n, _ in sizes))
+    assert raw.pg_workspace_bytes(arr, len(sizes)) == want
+    arr[2].n_leaves = 48
+    assert raw.pg_workspace_bytes(arr, len(sizes)) == 0
