@@ -8,6 +8,7 @@ import pytest
 
 import oracle
 import pg_synth
+from tree_check import check_tree_sampled
 
 torch = pytest.importorskip("torch")
 pg = pytest.importorskip("paper_2506_09505_gb300")
@@ -152,19 +153,7 @@ def test_merkle_wide_and_narrow_rows(w):
 
 
 def _check_tree_sampled(rows, out, seed, per_level=64):
-    n = rows.shape[0]
-    offs = pg.level_offsets(n)
-    assert (out < np.uint64(P)).all()
-    leaves = np.unique(np.concatenate([pg_synth.integers(seed, 256, 0, n - 1), [0, n - 1]]))
-    assert (out[leaves] == oracle.hash_rows(rows[leaves])).all()
-    cnt = n // 2
-    for lvl in range(1, len(offs)):
-        ks = np.unique(np.concatenate([pg_synth.integers(seed + lvl, per_level, 0, cnt - 1), [0, cnt - 1]]))
-        for k in ks:
-            left = out[offs[lvl - 1] + 2 * k]
-            right = out[offs[lvl - 1] + 2 * k + 1]
-            assert (out[offs[lvl] + k] == oracle.hash_pair(left, right)).all(), (lvl, k)
-        cnt //= 2
+    check_tree_sampled(rows, out, seed, per_level=per_level)
 
 
 @pytest.mark.parametrize("w", [8, 64])
