@@ -141,6 +141,44 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------ oracle timing
+def host_cpu_model() -> str:
+    """lscpu's model name of the host (or /proc/cpuinfo's), for the CPU baseline."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith(("model name", "cpu part")):
+                    return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def oracle_permute_rates(seconds=4.0):
+    """Single-thread and all-core permutations/s of the CPU oracle on random states."""
+    import oracle
+    import pg_synth
+    cores = os.cpu_count() or 1
+    out = {}
+    for label, threads in (("single_thread", 1), ("all_core", cores)):
+        n = 256 * threads
+        while True:
+            st = pg_synth.matrix(0x5EED0002, n, 12)
+            t0 = time.perf_counter()
+            oracle.permute(st, nthreads=threads)
+            dt = time.perf_counter() - t0
+            if dt >= seconds / 4 or n >= (1 << 22):
+                out[label] = {"perms_per_s": n / dt, "threads": threads, "sample_states": n, "seconds": dt}
+                break
+            n *= 4
+    return out
+
 def oracle_rate(width, seconds, seed=0x5EED0003):
     """Permutations/s of the CPU oracle (all host cores) on a bounded tree."""
     import numpy as np  # noqa: F401
@@ -200,7 +238,8 @@ def run_reference(args):
         "config": {"workload": name, "leaves": n, "width": args.width,
                    "parallelism": "cpu oracle, level-parallel threads"},
         "cpu_baseline": {"value": value, "unit": "perms/s", "cores": cores, "kind": "oracle",
-                         "sample": sample},
+                         "sample": sample, "host_cpu": host_cpu_model(),
+                         "ms_per_step_std": 1e3 * statistics.pstdev(times) if len(times) > 1 else 0.0},
         "e2e": {"value": value, "unit": "perms/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -337,7 +376,8 @@ def run_ours(args):
         rate, cores, log_s, dt, sp = oracle_rate(args.width, args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate, "unit": "perms/s", "cores": cores, "kind": "oracle",
                                 "sample": f"2^{log_s}-leaf tree of width {args.width} "
-                                          f"({sp} permutations, {dt:.1f} s), level-parallel threads"}
+                                          f"({sp} permutations, {dt:.1f} s), level-parallel threads",
+                                "host_cpu": host_cpu_model()}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -383,11 +423,19 @@ def run_permute(args):
     ms = e0.elapsed_time(e1) / args.steps
     rate = n / (ms / 1e3)
     ach = rate * (MUL_RESULTS_PER_PERM_SMALL if args.params == "pg12_small" else MUL_RESULTS_PER_PERM)
-    print(json.dumps({"workload": "permute 2^24 states in place", "params": args.params or "pg12_v1",
-                      "metric": "perms/s", "value": rate,
-                      "ms_per_step": ms, "steps": args.steps, "kernel": "k_permute",
-                      "roofline": {"bound": "alu", "achieved": ach / 1e12, "peak": _peak_results_per_s() / 1e12,
-                                   "unit": "T mul32-results/s", "frac": ach / _peak_results_per_s()}}), flush=True)
+    line = {"workload": "permute 2^24 states in place", "params": args.params or "pg12_v1",
+            "metric": "perms/s", "value": rate,
+            "ms_per_step": ms, "steps": args.steps, "kernel": "k_permute",
+            "roofline": {"bound": "alu", "achieved": ach / 1e12, "peak": _peak_results_per_s() / 1e12,
+                         "unit": "T mul32-results/s", "frac": ach / _peak_results_per_s()}}
+    if not args.no_cpu_baseline and not args.params:
+        rates = oracle_permute_rates()
+        line["cpu_baseline"] = {"value": rates["all_core"]["perms_per_s"], "unit": "perms/s",
+                                "cores": rates["all_core"]["threads"], "kind": "oracle",
+                                "sample": f"{rates['all_core']['sample_states']} random states, plain round form",
+                                "single_thread_perms_per_s": rates["single_thread"]["perms_per_s"],
+                                "host_cpu": host_cpu_model()}
+    print(json.dumps(line), flush=True)
     return 0
 
 

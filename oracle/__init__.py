@@ -62,6 +62,7 @@ def _load():
         "orc_permute": (None, [_u64p, _u64p, _u64p]),
         "orc_permute_inverse": (None, [_u64p, _u64p, _u64p]),
         "orc_permute_many": (None, [_u64p, _u64p, _u64p, sz]),
+        "orc_permute_many_mt": (None, [_u64p, _u64p, _u64p, sz, i]),
         "orc_hash_row": (None, [_u64p, _u64p, _u64p, sz, _u64p]),
         "orc_hash_pair": (None, [_u64p, _u64p, _u64p, _u64p, _u64p]),
         "orc_merkle_build": (i, [_u64p, _u64p, _u64p, sz, sz, _u64p, i]),
@@ -206,12 +207,15 @@ def _rc_mds(rc, mds):
 
 # ---------------------------------------------------------------- permutation
 
-def permute(states, rc=None, mds=None) -> np.ndarray:
+def permute(states, rc=None, mds=None, nthreads: int = 1) -> np.ndarray:
     """Plain-form Poseidon-12 on an array of states shaped (..., 12)."""
     rc, mds = _rc_mds(rc, mds)
     st = _u64(states).copy()
     flat = st.reshape(-1, T)
-    _load().orc_permute_many(_ptr(rc), _ptr(mds), _ptr(flat), flat.shape[0])
+    if nthreads > 1:
+        _load().orc_permute_many_mt(_ptr(rc), _ptr(mds), _ptr(flat), flat.shape[0], nthreads)
+    else:
+        _load().orc_permute_many(_ptr(rc), _ptr(mds), _ptr(flat), flat.shape[0])
     return flat.reshape(st.shape)
 
 

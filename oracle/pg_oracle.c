@@ -304,6 +304,41 @@ void orc_permute_many(const uint64_t *rc, const uint64_t *mds, uint64_t *st, siz
     for (size_t k = 0; k < n; k++) orc_permute(rc, mds, st + ORC_T * k);
 }
 
+typedef struct {
+    const uint64_t *rc, *mds;
+    uint64_t *st;
+    size_t lo, hi;
+} orc_perm_job;
+
+static void *orc_perm_worker(void *arg) {
+    orc_perm_job *j = (orc_perm_job *)arg;
+    for (size_t k = j->lo; k < j->hi; k++) orc_permute(j->rc, j->mds, j->st + ORC_T * k);
+    return NULL;
+}
+
+/* The same over nthreads threads, each taking a contiguous range of states
+ * (the timed all-core CPU baseline; the result equals orc_permute_many). */
+void orc_permute_many_mt(const uint64_t *rc, const uint64_t *mds, uint64_t *st, size_t n, int nthreads) {
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > 256) nthreads = 256;
+    if ((size_t)nthreads > n) nthreads = (int)(n ? n : 1);
+    pthread_t th[256];
+    orc_perm_job jobs[256];
+    for (int t = 0; t < nthreads; t++) {
+        jobs[t].rc = rc;
+        jobs[t].mds = mds;
+        jobs[t].st = st;
+        jobs[t].lo = n * (size_t)t / (size_t)nthreads;
+        jobs[t].hi = n * (size_t)(t + 1) / (size_t)nthreads;
+    }
+    if (nthreads == 1) {
+        orc_perm_worker(&jobs[0]);
+        return;
+    }
+    for (int t = 0; t < nthreads; t++) pthread_create(&th[t], NULL, orc_perm_worker, &jobs[t]);
+    for (int t = 0; t < nthreads; t++) pthread_join(th[t], NULL);
+}
+
 /* ----------------------------------------------------------------- sponge */
 
 /* Overwrite-mode sponge, rate 8 / capacity 4, digest = state[0..3].

@@ -394,6 +394,11 @@ def test_merkle_threads_match_single_thread():
     assert (oracle.merkle_build(rows, nthreads=1) == oracle.merkle_build(rows, nthreads=4)).all()
 
 
+def test_permute_threads_match_single_thread():
+    st = pg_synth.matrix(0x3A1, 301, 12)
+    assert (oracle.permute(st, nthreads=7) == oracle.permute(st)).all()
+
+
 def test_merkle_subtree_split_recombines():
     # sharding invariant: G subtrees built apart, top levels hashed from their
     # roots, equals the whole tree
