@@ -38,10 +38,22 @@ MUL_RESULTS_PER_PERM = 118 * (2 * 6 + 2 * 8) + 8 * 144 * 8 + 22 * 23 * 8
 # IMAD.WIDE per term (4 results); round 3's transition matrix stays full width.
 MUL_RESULTS_PER_PERM_SMALL = 118 * (2 * 6 + 2 * 8) + 7 * 144 * 4 + 144 * 8 + 22 * 23 * 8
 IMAD_RESULTS_PER_CLK_SM = 64  # 32-bit multiply results per clock per SM
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_merkle
-# launch, from one ncu capture of the current kernel on that workload
-# (params, log2 leaves, width); other workloads report null.
-K_MERKLE_TRAFFIC = {("pg12_v1", 22, 8): 273_648_128 + 224_156_928}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of each
+# kernel of a tree build, averaged over its launches in one ncu capture of the
+# current kernels on that workload (params, log2 leaves, width); other
+# workloads report null.
+KERNEL_TRAFFIC = {("pg12_v1", 22, 8, "k_merkle"): 369_402_445,
+                  ("pg12_v1", 22, 8, "k_hash_rows"): 37_468_877,
+                  ("pg12_v1", 22, 8, "k_merkle_top"): 100_299}
+
+
+def algorithmic_bytes(kernel, perms_per_launch, width):
+    """Bytes a launch must move: rows read and digests written (leaves), or two
+    child digests read and one written per node (levels)."""
+    if kernel in ("k_merkle", "k_merkle_top_leaf"):
+        leaves = perms_per_launch // max(1, (width + 7) // 8)
+        return leaves * (8 * width + 32)
+    return perms_per_launch * 96
 
 
 def parse_args():
@@ -337,24 +349,36 @@ def run_ours(args):
     max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     peak = IMAD_RESULTS_PER_CLK_SM * sms * max_mhz * 1e6 / 1e12  # T results/s
     dropped = kernels.pop("_dropped", 0)
-    km = kernels["k_merkle"]
-    km_ms = km["total_ms"] / km["launches"]          # average k_merkle launch, event-timed
-    km_perms = km["perms"] // km["launches"]         # its permutations per launch
-    achieved = km_perms * mul_per_perm / (km_ms / 1e3) / 1e12
     tot_kernel_ms = sum(v["total_ms"] for v in kernels.values())
+
+    def kernel_roofline(name):
+        v = kernels[name]
+        launch_ms = v["total_ms"] / v["launches"]      # average launch, event-timed
+        per_launch = v["perms"] // v["launches"]       # permutations per launch
+        ach = per_launch * mul_per_perm / (launch_ms / 1e3) / 1e12
+        return {"achieved": ach, "frac": ach / peak, "launch_ms": launch_ms, "perms_per_launch": per_launch,
+                "mul32_results_per_launch": per_launch * mul_per_perm,
+                "algorithmic_bytes_per_launch": algorithmic_bytes(name, per_launch, args.width),
+                "traffic": KERNEL_TRAFFIC.get((args.params or "pg12_v1", args.log_n, args.width, name))}
+
+    dom = max(kernels, key=lambda k: kernels[k]["total_ms"])   # the kernel with the largest share
+    rk = kernel_roofline(dom)
     roofline = {
-        "bound": "alu", "kernel": "k_merkle",
-        "achieved": achieved, "peak": peak, "unit": "T mul32-results/s",
-        "frac": achieved / peak,
+        "bound": "alu", "kernel": dom,
+        "achieved": rk["achieved"], "peak": peak, "unit": "T mul32-results/s",
+        "frac": rk["frac"],
         "peak_basis": f"{IMAD_RESULTS_PER_CLK_SM} x {sms} SMs x {max_mhz:.0f} MHz (sm_max_mhz)",
-        "traffic": K_MERKLE_TRAFFIC.get((args.params or "pg12_v1", args.log_n, args.width)),
-        "launch_ms": km_ms, "perms_per_launch": km_perms,
-        "mul32_results_per_launch": km_perms * mul_per_perm,
+        "traffic": rk["traffic"],
+        "launch_ms": rk["launch_ms"], "perms_per_launch": rk["perms_per_launch"],
+        "mul32_results_per_launch": rk["mul32_results_per_launch"],
+        "algorithmic_bytes_per_launch": rk["algorithmic_bytes_per_launch"],
         "step_frac": perms * mul_per_perm / (ms / 1e3) / 1e12 / peak,
-        "algorithmic_bytes_per_launch": int(rows_np.nbytes + 32 * (2 * n - 1)),
+        "per_kernel": {k: {"frac": r["frac"], "launch_ms": r["launch_ms"], "traffic": r["traffic"],
+                           "algorithmic_bytes_per_launch": r["algorithmic_bytes_per_launch"]}
+                       for k, r in ((k, kernel_roofline(k)) for k in kernels)},
     }
     if clocks and clocks.get("sm_mhz"):
-        roofline["frac_at_sampled_clock"] = achieved / (IMAD_RESULTS_PER_CLK_SM * sms * clocks["sm_mhz"] * 1e6 / 1e12)
+        roofline["frac_at_sampled_clock"] = rk["achieved"] / (IMAD_RESULTS_PER_CLK_SM * sms * clocks["sm_mhz"] * 1e6 / 1e12)
 
     line = {
         "metric": METRIC, "value": value, "unit": "perms/s", "n_gpus": world,

@@ -222,7 +222,10 @@ pg_status pg_hash_rows(const uint64_t *rows, size_t n_rows, size_t width, uint64
  *             of nodes 2k and 2k+1 of level l-1.
  *   root_out  host, 4 words, or NULL.  When non-NULL the call synchronises
  *             `stream` and copies the root there.
- * Uses the library workspace (allocated in pg_init) for its tile counters;
+ * Launches: the leaf sponges in the persistent kernel, then one launch per
+ * level (trees of at most 8,192 leaves: one launch for the leaves and one per
+ * level, all in the 16-lanes-per-state form).
+ * Uses the library workspace (allocated in pg_init) for its task counter;
  * concurrent builds on different streams are not supported.
  */
 pg_status pg_merkle_build(const uint64_t *rows, size_t n_leaves, size_t width, uint64_t *nodes,

@@ -454,10 +454,24 @@ namespace {
     } while (0)
 
 constexpr size_t kWorkspaceBytes = 32u << 20;  // tree plans + arrival counters
+// pg_merkle_build's split of a tree between kernels.  Trees of at most
+// kSmallTree leaves run entirely in the 16-lanes-per-state kernels.  In
+// larger trees the persistent kernel builds the levels with more than
+// kTopNodes nodes (by default only the leaves: one launch per level measured
+// faster than climbing with arrival counters, 16.7 against 17.4 ms for a
+// 2^22 x 8 tree), and every other level is one launch: one thread per node
+// (k_hash_rows over the children, since a node is the sponge of its
+// children's eight words) while the level has more than kWideNodes nodes,
+// the 16-lanes-per-state kernel above that.
 #ifndef PG12_TOP_NODES
-#define PG12_TOP_NODES 32768
+#define PG12_TOP_NODES (1ull << 40)
 #endif
-constexpr uint64_t kTopNodes = PG12_TOP_NODES;  // levels this small use the wide kernel
+constexpr uint64_t kTopNodes = PG12_TOP_NODES;
+#ifndef PG12_WIDE_NODES
+#define PG12_WIDE_NODES 8192
+#endif
+constexpr uint64_t kWideNodes = PG12_WIDE_NODES;
+constexpr uint64_t kSmallTree = kWideNodes;
 constexpr size_t kPlanBytes = 4u << 20;        // first part: plans; rest: counters
 
 // ------------------------------------------------------------ launch timing
@@ -1116,8 +1130,8 @@ pg_status pg_merkle_build(const uint64_t *rows, size_t n_leaves, size_t width, u
     std::memset(&tp, 0, sizeof tp);
     uint32_t n_counters = 0;
     const uint32_t tasks = plan_tree(tp, rows, n_leaves, width, nodes, 0, 0, n_counters);
-    // levels with at most kTopNodes nodes are built by the low-latency
-    // 16-lanes-per-state kernel, one launch per level, after the persistent one
+    // levels with at most kTopNodes nodes are built one launch per level,
+    // after the persistent kernel
     uint32_t first_top = tp.log_n + 1;
     for (uint32_t l = 1; l <= tp.log_n; ++l)
         if ((n_leaves >> l) <= (uint64_t)kTopNodes) {
@@ -1129,7 +1143,8 @@ pg_status pg_merkle_build(const uint64_t *rows, size_t n_leaves, size_t width, u
     if (sizeof(tp) > kPlanBytes || counter_bytes > g.ws_bytes - kPlanBytes)
         return fail(PG_ERR_OOM, "workspace too small for %zu leaves", n_leaves);
     cudaStream_t st = as_stream(stream);
-    const bool small = (uint64_t)n_leaves <= kTopNodes;  // whole tree in the wide form
+    const bool small = (uint64_t)n_leaves <= kSmallTree;  // whole tree in the wide form
+    if (small) first_top = 1;
     auto *d_plan = reinterpret_cast<dev::TreePlan *>(g.ws);
     auto *d_counters = reinterpret_cast<uint32_t *>(g.ws + kPlanBytes);
     if (small) {
@@ -1140,17 +1155,29 @@ pg_status pg_merkle_build(const uint64_t *rows, size_t n_leaves, size_t width, u
         PG_CUDA(cudaGetLastError());
     } else {
         PG_CUDA(cudaMemcpyAsync(d_plan, &tp, sizeof tp, cudaMemcpyHostToDevice, st));
-        PG_CUDA(cudaMemsetAsync(d_counters, 0, counter_bytes, st));
+        // the task counter, plus the arrival counters when the kernel climbs
+        PG_CUDA(cudaMemsetAsync(d_counters, 0, tp.climb_limit ? counter_bytes : sizeof(uint32_t), st));
         // leaf sponges plus the nodes of levels 1 .. first_top-1
         const uint64_t perms = tree_perms(n_leaves, width) - ((n_leaves >> (first_top - 1)) - 1);
         s = launch_merkle(nullptr, d_plan, 1u, tasks, d_counters, st, perms);
         if (s != PG_OK) return s;
     }
     for (uint32_t l = first_top; l <= tp.log_n; ++l) {
-        const uint64_t threads = (n_leaves >> l) * 16;
-        const unsigned grid = (unsigned)((threads + dev::kTopBlock - 1) / dev::kTopBlock);
-        ProfScope prof(kIdMerkleTop, st, (uint64_t)n_leaves >> l);
-        dev::k_merkle_top<<<grid, dev::kTopBlock, 0, st>>>(nodes, (uint64_t)n_leaves, l);
+        const uint64_t cnt = (uint64_t)n_leaves >> l;
+        if (cnt > kWideNodes) {
+            const uint64_t *below = nodes + 4 * (2 * (uint64_t)n_leaves - (2 * (uint64_t)n_leaves >> (l - 1)));
+            uint64_t *here = nodes + 4 * (2 * (uint64_t)n_leaves - (2 * (uint64_t)n_leaves >> l));
+            const unsigned grid = (unsigned)((cnt + 127) / 128);
+            ProfScope prof(kIdHashRows, st, cnt);
+            if (g.params_set == 1)
+                dev::k_hash_rows<dev::kMdsSmall><<<grid, 128, 0, st>>>(below, cnt, 8, 1, here);
+            else
+                dev::k_hash_rows<dev::kMdsFull><<<grid, 128, 0, st>>>(below, cnt, 8, 1, here);
+        } else {
+            const unsigned grid = (unsigned)((cnt * 16 + dev::kTopBlock - 1) / dev::kTopBlock);
+            ProfScope prof(kIdMerkleTop, st, cnt);
+            dev::k_merkle_top<<<grid, dev::kTopBlock, 0, st>>>(nodes, (uint64_t)n_leaves, l);
+        }
         PG_CUDA(cudaGetLastError());
     }
     if (root_out) {
