@@ -232,6 +232,23 @@ pg_status pg_merkle_build(const uint64_t *rows, size_t n_leaves, size_t width, u
                           uint64_t *root_out, void *stream);
 
 /*
+ * pg_merkle_build_host -- pg_merkle_build with the rows in host memory: the
+ * same nodes, with the host-to-device copy of the rows overlapped with leaf
+ * hashing (the rows are copied in up to 16 chunks on a library stream and
+ * each chunk's leaves are hashed on `stream` as soon as it has arrived).
+ *   rows_host  host, n_leaves*width words, row-major; page-locked memory
+ *              lets the copies overlap (pageable memory works, serialised).
+ *   rows_dev   dev, n_leaves*width words: caller-owned staging buffer the
+ *              rows are copied into (holds them on return).
+ *   n_leaves, width, nodes, root_out, stream  as for pg_merkle_build.
+ * The copies start once the work already queued on `stream` has finished.
+ * Allocates nothing.  Calls from several host threads at once are not
+ * supported (they share the library's copy stream and events).
+ */
+pg_status pg_merkle_build_host(const uint64_t *rows_host, size_t n_leaves, size_t width, uint64_t *rows_dev,
+                               uint64_t *nodes, uint64_t *root_out, void *stream);
+
+/*
  * pg_merkle_build_batch -- Sec. 4.2 trees of mixed sizes and widths built
  * in ONE persistent launch: leaf tasks of all trees come from one counter
  * and each tree's upper levels are built by the warp that completes the

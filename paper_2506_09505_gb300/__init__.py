@@ -113,6 +113,8 @@ SIGNATURES = {
                                      ctypes.c_size_t, ctypes.c_void_p]),
     "pg_field_bench": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                       ctypes.POINTER(ctypes.c_double)]),
+    "pg_merkle_build_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_size_t, ctypes.c_void_p,
+                                            ctypes.c_void_p, _u64p, ctypes.c_void_p]),
     "pg_params_sha256": (ctypes.c_char_p, []),
     "pg_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(Tree), ctypes.c_size_t]),
     "pg_ntt": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p]),
@@ -259,6 +261,31 @@ def merkle_build(rows, nodes=None, want_root: bool = False, stream=None):
     _check(load().pg_merkle_build(_dev_ptr(rows, "rows"), n, w, _dev_ptr(nodes, "nodes"),
                                   ctypes.cast(root, _u64p) if want_root else None,
                                   _stream(stream)))
+    if want_root:
+        return nodes, [int(v) for v in root]
+    return nodes
+
+
+def merkle_build_host(rows_host, rows_dev=None, nodes=None, want_root: bool = False, stream=None):
+    """Tree over the (N, w) int64 rows of a host tensor (page-locked for overlap): the rows are
+    copied into ``rows_dev`` (a CUDA staging tensor of the same shape, allocated when not given)
+    in chunks while earlier chunks are hashed.  Returns nodes, or (nodes, root) with want_root."""
+    import torch
+    if rows_host.dim() != 2 or rows_host.is_cuda:
+        raise ValueError("rows_host must be a (N, w) host tensor")
+    if rows_host.dtype not in (torch.int64, torch.uint64) or not rows_host.is_contiguous():
+        raise TypeError("rows_host must be a contiguous 64-bit tensor")
+    n, w = rows_host.shape
+    if rows_dev is None:
+        rows_dev = torch.empty((n, w), dtype=rows_host.dtype, device="cuda")
+    if tuple(rows_dev.shape) != (n, w):
+        raise ValueError("rows_dev must have the shape of rows_host")
+    if nodes is None:
+        nodes = torch.empty((2 * n - 1, DIGEST), dtype=torch.int64, device=rows_dev.device)
+    root = (ctypes.c_uint64 * 4)() if want_root else None
+    _check(load().pg_merkle_build_host(rows_host.data_ptr(), n, w, _dev_ptr(rows_dev, "rows_dev"),
+                                       _dev_ptr(nodes, "nodes"),
+                                       ctypes.cast(root, _u64p) if want_root else None, _stream(stream)))
     if want_root:
         return nodes, [int(v) for v in root]
     return nodes

@@ -422,6 +422,8 @@ struct Context {
     int permute_blocks_per_sm = 0;
     uint8_t *ws = nullptr;  // device workspace
     size_t ws_bytes = 0;
+    cudaStream_t copy_st = nullptr;  // host-row copies of pg_merkle_build_host
+    cudaEvent_t host_ev[17] = {};    // one per chunk, plus "previous work done"
 };
 Context g;
 std::mutex g_mu;
@@ -615,6 +617,45 @@ pg_status plan_batch(const pg_tree *trees, size_t n_trees, const pg_schedule *sc
     }
     tasks = (uint32_t)task_sum;
     counters = counter_sum;
+    return PG_OK;
+}
+
+// One launch per level for levels first..log2(n_leaves) of a tree whose
+// lower levels are in `nodes`: one thread per node while a level has more
+// than kWideNodes nodes, the 16-lanes-per-state kernel above that.
+pg_status launch_levels(uint64_t *nodes, uint64_t n_leaves, uint32_t first, cudaStream_t st) {
+    const uint32_t log_n = log2u(n_leaves);
+    for (uint32_t l = first; l <= log_n; ++l) {
+        const uint64_t cnt = n_leaves >> l;
+        if (cnt > kWideNodes) {
+            const uint64_t *below = nodes + 4 * (2 * n_leaves - ((2 * n_leaves) >> (l - 1)));
+            uint64_t *here = nodes + 4 * (2 * n_leaves - ((2 * n_leaves) >> l));
+            const unsigned grid = (unsigned)((cnt + 127) / 128);
+            ProfScope prof(kIdHashRows, st, cnt);
+            if (g.params_set == 1)
+                dev::k_hash_rows<dev::kMdsSmall><<<grid, 128, 0, st>>>(below, cnt, 8, 1, here);
+            else
+                dev::k_hash_rows<dev::kMdsFull><<<grid, 128, 0, st>>>(below, cnt, 8, 1, here);
+        } else {
+            const unsigned grid = (unsigned)((cnt * 16 + dev::kTopBlock - 1) / dev::kTopBlock);
+            ProfScope prof(kIdMerkleTop, st, cnt);
+            dev::k_merkle_top<<<grid, dev::kTopBlock, 0, st>>>(nodes, n_leaves, l);
+        }
+        PG_CUDA(cudaGetLastError());
+    }
+    return PG_OK;
+}
+
+// Leaf digests of rows[0 .. n) on `st` (k_hash_rows, grid capped like pg_hash_rows).
+pg_status launch_leaves(const uint64_t *rows, uint64_t n, uint64_t width, uint64_t *digests, cudaStream_t st) {
+    const int vec16 = ((width % 2) == 0 && (reinterpret_cast<uintptr_t>(rows) % 16) == 0) ? 1 : 0;
+    const uint64_t want = (n + 127) / 128;
+    const uint64_t cap = (uint64_t)g.sms * g.permute_blocks_per_sm * 8;
+    const unsigned grid = (unsigned)(want < cap ? want : cap);
+    ProfScope prof(kIdHashRows, st, n * ((width + kRate - 1) / kRate));
+    if (g.params_set == 1) dev::k_hash_rows<dev::kMdsSmall><<<grid, 128, 0, st>>>(rows, n, width, vec16, digests);
+    else dev::k_hash_rows<dev::kMdsFull><<<grid, 128, 0, st>>>(rows, n, width, vec16, digests);
+    PG_CUDA(cudaGetLastError());
     return PG_OK;
 }
 
@@ -1062,6 +1103,8 @@ pg_status pg_init(int device, const char *params_path) {
     if (e != cudaSuccess) return fail(PG_ERR_OOM, "workspace cudaMalloc(%zu): %s", kWorkspaceBytes, cudaGetErrorString(e));
     g.ws = static_cast<uint8_t *>(ws);
     g.ws_bytes = kWorkspaceBytes;
+    PG_CUDA(cudaStreamCreateWithFlags(&g.copy_st, cudaStreamNonBlocking));
+    for (auto &ev : g.host_ev) PG_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
     g.device = device;
     g.init = true;
     return PG_OK;
@@ -1073,6 +1116,12 @@ pg_status pg_shutdown(void) {
     cudaSetDevice(g.device);
     if (g.ws) cudaFree(g.ws);
     g.ws = nullptr;
+    if (g.copy_st) cudaStreamDestroy(g.copy_st);
+    g.copy_st = nullptr;
+    for (auto &ev : g.host_ev) {
+        if (ev) cudaEventDestroy(ev);
+        ev = nullptr;
+    }
     g.init = false;
     g.device = -1;
     return PG_OK;
@@ -1162,26 +1211,52 @@ pg_status pg_merkle_build(const uint64_t *rows, size_t n_leaves, size_t width, u
         s = launch_merkle(nullptr, d_plan, 1u, tasks, d_counters, st, perms);
         if (s != PG_OK) return s;
     }
-    for (uint32_t l = first_top; l <= tp.log_n; ++l) {
-        const uint64_t cnt = (uint64_t)n_leaves >> l;
-        if (cnt > kWideNodes) {
-            const uint64_t *below = nodes + 4 * (2 * (uint64_t)n_leaves - (2 * (uint64_t)n_leaves >> (l - 1)));
-            uint64_t *here = nodes + 4 * (2 * (uint64_t)n_leaves - (2 * (uint64_t)n_leaves >> l));
-            const unsigned grid = (unsigned)((cnt + 127) / 128);
-            ProfScope prof(kIdHashRows, st, cnt);
-            if (g.params_set == 1)
-                dev::k_hash_rows<dev::kMdsSmall><<<grid, 128, 0, st>>>(below, cnt, 8, 1, here);
-            else
-                dev::k_hash_rows<dev::kMdsFull><<<grid, 128, 0, st>>>(below, cnt, 8, 1, here);
-        } else {
-            const unsigned grid = (unsigned)((cnt * 16 + dev::kTopBlock - 1) / dev::kTopBlock);
-            ProfScope prof(kIdMerkleTop, st, cnt);
-            dev::k_merkle_top<<<grid, dev::kTopBlock, 0, st>>>(nodes, (uint64_t)n_leaves, l);
-        }
-        PG_CUDA(cudaGetLastError());
-    }
+    s = launch_levels(nodes, n_leaves, first_top, st);
+    if (s != PG_OK) return s;
     if (root_out) {
         PG_CUDA(cudaMemcpyAsync(root_out, nodes + 4 * (2 * n_leaves - 2), 32, cudaMemcpyDeviceToHost, st));
+        PG_CUDA(cudaStreamSynchronize(st));
+    }
+    return PG_OK;
+}
+
+pg_status pg_merkle_build_host(const uint64_t *rows_host, size_t n_leaves, size_t width, uint64_t *rows_dev,
+                               uint64_t *nodes, uint64_t *root_out, void *stream) {
+    pg_status s = require_init();
+    if (s != PG_OK) return s;
+    if (!rows_host || !rows_dev || !nodes) return fail(PG_ERR_INVALID_ARG, "rows_host, rows_dev or nodes is NULL");
+    if (width == 0) return fail(PG_ERR_INVALID_ARG, "width must be >= 1");
+    if (!is_pow2(n_leaves)) return fail(PG_ERR_NOT_POW2, "n_leaves=%zu is not a power of two", n_leaves);
+    if (n_leaves > (1ull << 34)) return fail(PG_ERR_INVALID_ARG, "n_leaves=%zu above 2^34", n_leaves);
+    if (reinterpret_cast<uintptr_t>(rows_dev) % 8) return fail(PG_ERR_INVALID_ARG, "rows_dev not 8-byte aligned");
+    if (reinterpret_cast<uintptr_t>(nodes) % 16) return fail(PG_ERR_INVALID_ARG, "nodes not 16-byte aligned");
+    cudaStream_t st = as_stream(stream);
+    const uint64_t n = n_leaves, bytes_per_row = 8 * (uint64_t)width;
+    if (n <= kSmallTree) {
+        PG_CUDA(cudaMemcpyAsync(rows_dev, rows_host, n * bytes_per_row, cudaMemcpyHostToDevice, st));
+        return pg_merkle_build(rows_dev, n_leaves, width, nodes, root_out, stream);
+    }
+    // chunks of at least 2^18 rows, at most 16 of them
+    uint64_t chunk = 1ull << 18;
+    while (n / chunk > 16) chunk <<= 1;
+    if (chunk > n) chunk = n;
+    const uint32_t k_chunks = (uint32_t)(n / chunk);
+    // the copies into rows_dev wait for work already queued on `st` (an earlier build may still read it)
+    PG_CUDA(cudaEventRecord(g.host_ev[16], st));
+    PG_CUDA(cudaStreamWaitEvent(g.copy_st, g.host_ev[16], 0));
+    for (uint32_t c = 0; c < k_chunks; ++c) {
+        const uint64_t first = (uint64_t)c * chunk;
+        PG_CUDA(cudaMemcpyAsync(rows_dev + first * width, rows_host + first * width, chunk * bytes_per_row,
+                                cudaMemcpyHostToDevice, g.copy_st));
+        PG_CUDA(cudaEventRecord(g.host_ev[c], g.copy_st));
+        PG_CUDA(cudaStreamWaitEvent(st, g.host_ev[c], 0));
+        s = launch_leaves(rows_dev + first * width, chunk, width, nodes + 4 * first, st);
+        if (s != PG_OK) return s;
+    }
+    s = launch_levels(nodes, n, 1, st);
+    if (s != PG_OK) return s;
+    if (root_out) {
+        PG_CUDA(cudaMemcpyAsync(root_out, nodes + 4 * (2 * n - 2), 32, cudaMemcpyDeviceToHost, st));
         PG_CUDA(cudaStreamSynchronize(st));
     }
     return PG_OK;
