@@ -73,27 +73,44 @@ __device__ Consts g_ntt;
 __device__ __forceinline__ uint64_t mul_c(uint64_t a, uint64_t b) { return canon(mul(a, b)); }
 
 // Weak operands and results (any 64-bit word standing for its residue).  A
-// carry out of bit 63 is worth 2^64 = 2^32 - 1 (mod p); adding it can carry
-// once more only when both inputs were near 2^64, and then the sum is tiny.
+// carry out of bit 63 is worth 2^64 = 2^32 - 1 (mod p); adding it back can
+// carry once more only when both inputs were near 2^64, and then the sum is
+// below 2^33.  The carry itself becomes the 32-bit mask 0 - carry (0 or
+// 2^32 - 1), so no compare or select is needed.
 __device__ __forceinline__ uint64_t add_w(uint64_t a, uint64_t b) {
-    uint64_t s = a + b;
-    if (s < b) {
-        s += dev::EPS;
-        if (s < dev::EPS) s += dev::EPS;
-    }
-    return s;
+    uint32_t s0, s1, m;
+    asm("add.cc.u32 %0, %3, %5;\n\t"
+        "addc.cc.u32 %1, %4, %6;\n\t"
+        "addc.u32 %2, 0, 0;\n\t"
+        "sub.u32 %2, 0, %2;\n\t"
+        "add.cc.u32 %0, %0, %2;\n\t"
+        "addc.cc.u32 %1, %1, 0;\n\t"
+        "addc.u32 %2, 0, 0;\n\t"
+        "sub.u32 %2, 0, %2;\n\t"
+        "add.cc.u32 %0, %0, %2;\n\t"
+        "addc.u32 %1, %1, 0;"
+        : "=r"(s0), "=r"(s1), "=r"(m)
+        : "r"(dev::lo32(a)), "r"(dev::hi32(a)), "r"(dev::lo32(b)), "r"(dev::hi32(b)));
+    return ((uint64_t)s1 << 32) | s0;
 }
-// A borrow is worth -(2^32 - 1); subtracting it borrows again only when the
-// difference was within 2^32 - 1 of -2^64, and then twice is enough.
+// A borrow is worth -(2^32 - 1): subtracting it borrows again only when the
+// difference was within 2^32 - 1 of -2^64, and then twice is enough.  The
+// borrow-out of subc (0 - 0 - borrow) is already the mask.
 __device__ __forceinline__ uint64_t sub_w(uint64_t a, uint64_t b) {
-    uint64_t d = a - b;
-    if (a < b) {
-        const uint64_t e = d;
-        d -= dev::EPS;
-        if (e < dev::EPS) d -= dev::EPS;
-    }
-    return d;
+    uint32_t d0, d1, m;
+    asm("sub.cc.u32 %0, %3, %5;\n\t"
+        "subc.cc.u32 %1, %4, %6;\n\t"
+        "subc.u32 %2, 0, 0;\n\t"
+        "sub.cc.u32 %0, %0, %2;\n\t"
+        "subc.cc.u32 %1, %1, 0;\n\t"
+        "subc.u32 %2, 0, 0;\n\t"
+        "sub.cc.u32 %0, %0, %2;\n\t"
+        "subc.u32 %1, %1, 0;"
+        : "=r"(d0), "=r"(d1), "=r"(m)
+        : "r"(dev::lo32(a)), "r"(dev::hi32(a)), "r"(dev::lo32(b)), "r"(dev::hi32(b)));
+    return ((uint64_t)d1 << 32) | d0;
 }
+
 // x^e for a 30-bit exponent from three 10-bit digit tables
 __device__ __forceinline__ uint64_t pow_tab(const uint64_t (*t)[1024], uint64_t e) {
     return mul_c(mul_c(t[0][e & 1023], t[1][(e >> 10) & 1023]), t[2][(e >> 20) & 1023]);
