@@ -1,13 +1,16 @@
 // Kernels and C ABI of the GB300 Poseidon-12 / Goldilocks Merkle library.
 //
 //   k_permute   Alg. 1 on a batch of independent states, one thread each.
-//   k_hash_rows Sec. 2.4 sponge (rate 8, capacity 4, overwrite mode) per row.
-//   k_merkle    Sec. 4.2 tree build as one persistent launch: warps pull
-//               32-leaf tasks from a global counter and hash those rows; the
-//               warp that completes the second of two sibling 32-node groups
-//               (an atomic arrival counter, never a spin) goes on to hash
-//               their 32 parents, so the upper levels start as soon as their
-//               subtree is ready instead of after a grid-wide barrier.
+//   k_hash_rows Sec. 2.4 sponge (rate 8, capacity 4, overwrite mode) per row;
+//               also a whole tree level (a node is the sponge of its
+//               children's eight words).
+//   k_merkle    Sec. 4.2 persistent tree kernel: warps pull 32-leaf tasks
+//               from a global counter and hash those rows; up to a plan's
+//               climb limit, the warp that completes the second of two
+//               sibling 32-node groups (an atomic arrival counter, never a
+//               spin) goes on to hash their 32 parents.  Single trees use it
+//               for the leaves only (then one launch per level); batches
+//               climb to every tree's root.
 //   k_merkle_top / k_merkle_top_leaf
 //               the levels with few nodes, 16 lanes per state (latency form).
 //   k_merkle_open / k_merkle_verify  authentication paths (Sec. 2.4).
