@@ -234,7 +234,7 @@ pg_status pg_merkle_build(const uint64_t *rows, size_t n_leaves, size_t width, u
 /*
  * pg_merkle_build_host -- pg_merkle_build with the rows in host memory: the
  * same nodes, with the host-to-device copy of the rows overlapped with leaf
- * hashing (the rows are copied in up to 16 chunks on a library stream and
+ * hashing (the rows are copied in at most 11 growing chunks on a library stream and
  * each chunk's leaves are hashed on `stream` as soon as it has arrived).
  *   rows_host  host, n_leaves*width words, row-major; page-locked memory
  *              lets the copies overlap (pageable memory works, serialised).

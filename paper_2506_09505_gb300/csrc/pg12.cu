@@ -1239,22 +1239,26 @@ pg_status pg_merkle_build_host(const uint64_t *rows_host, size_t n_leaves, size_
         PG_CUDA(cudaMemcpyAsync(rows_dev, rows_host, n * bytes_per_row, cudaMemcpyHostToDevice, st));
         return pg_merkle_build(rows_dev, n_leaves, width, nodes, root_out, stream);
     }
-    // chunks of at least 2^18 rows, at most 16 of them
-    uint64_t chunk = 1ull << 18;
-    while (n / chunk > 16) chunk <<= 1;
-    if (chunk > n) chunk = n;
-    const uint32_t k_chunks = (uint32_t)(n / chunk);
-    // the copies into rows_dev wait for work already queued on `st` (an earlier build may still read it)
+    // Chunks grow geometrically: the first (n / 64 rows) is small so hashing
+    // starts early, each next one doubles up to n / 8.  A copy runs several
+    // times faster than hashing consumes rows, so every later chunk arrives
+    // before the one ahead of it is hashed; at most 11 chunks.
+    // The copies into rows_dev wait for work already queued on `st` (an
+    // earlier build may still read it).
     PG_CUDA(cudaEventRecord(g.host_ev[16], st));
     PG_CUDA(cudaStreamWaitEvent(g.copy_st, g.host_ev[16], 0));
-    for (uint32_t c = 0; c < k_chunks; ++c) {
-        const uint64_t first = (uint64_t)c * chunk;
-        PG_CUDA(cudaMemcpyAsync(rows_dev + first * width, rows_host + first * width, chunk * bytes_per_row,
+    const uint64_t chunk_max = n / 8;
+    uint64_t chunk = n / 64, first = 0;
+    for (uint32_t c = 0; first < n; ++c) {
+        const uint64_t rows_c = chunk < n - first ? chunk : n - first;
+        PG_CUDA(cudaMemcpyAsync(rows_dev + first * width, rows_host + first * width, rows_c * bytes_per_row,
                                 cudaMemcpyHostToDevice, g.copy_st));
         PG_CUDA(cudaEventRecord(g.host_ev[c], g.copy_st));
         PG_CUDA(cudaStreamWaitEvent(st, g.host_ev[c], 0));
-        s = launch_leaves(rows_dev + first * width, chunk, width, nodes + 4 * first, st);
+        s = launch_leaves(rows_dev + first * width, rows_c, width, nodes + 4 * first, st);
         if (s != PG_OK) return s;
+        first += rows_c;
+        if (chunk < chunk_max) chunk <<= 1;
     }
     s = launch_levels(nodes, n, 1, st);
     if (s != PG_OK) return s;
