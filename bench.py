@@ -331,17 +331,20 @@ def run_ours(args):
         pg.merkle_build_host(host_rows, dev_rows, nodes, want_root=True)
     barrier()
     e_steps = max(3, min(args.steps, 10))
+    e_sampler = ClockSampler(gpu_id)
+    time.sleep(0.4)
     t0 = time.perf_counter()
     for _ in range(e_steps):
         pg.merkle_build_host(host_rows, dev_rows, nodes, want_root=True)
     e_s = time.perf_counter() - t0
+    e_clocks = e_sampler.stop()
     if dist is not None:
         t = torch.tensor([e_s], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e_s = float(t.item())
     e2e = {"value": perms * world * e_steps / e_s, "unit": "perms/s",
            "h2d_bytes_per_step": int(rows_np.nbytes), "d2h_bytes_per_step": 32,
-           "ms_per_step": 1e3 * e_s / e_steps}
+           "ms_per_step": 1e3 * e_s / e_steps, "clocks": e_clocks}
 
     peaks = measured_peaks()
     sms = props.multi_processor_count
