@@ -532,7 +532,8 @@ pg_status ensure_params() {
     if (g.params_set == 1) host::generate_small(g.plain, g.small_row);
     else host::generate_plain(g.plain);
     if (!host::derive_optimized(g.plain, g.opt))
-        return fail(PG_ERR_PARAMS, "parameter set pg12_v1: sparse rewrite failed (singular block)");
+        return fail(PG_ERR_PARAMS, "parameter set %s: sparse rewrite failed (singular block)",
+                    g.params_set == 1 ? "pg12_small" : "pg12_v1");
     g.params_ready = true;
     return PG_OK;
 }
