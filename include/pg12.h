@@ -241,6 +241,7 @@ pg_status pg_merkle_build(const uint64_t *rows, size_t n_leaves, size_t width, u
  *   rows_dev   dev, n_leaves*width words: caller-owned staging buffer the
  *              rows are copied into (holds them on return).
  *   n_leaves, width, nodes, root_out, stream  as for pg_merkle_build.
+ * Rows of less than 64 MiB are copied in one piece before the build.
  * The copies start once the work already queued on `stream` has finished.
  * Allocates nothing.  Calls from several host threads at once are not
  * supported (they share the library's copy stream and events).

@@ -1236,7 +1236,9 @@ pg_status pg_merkle_build_host(const uint64_t *rows_host, size_t n_leaves, size_
     if (reinterpret_cast<uintptr_t>(nodes) % 16) return fail(PG_ERR_INVALID_ARG, "nodes not 16-byte aligned");
     cudaStream_t st = as_stream(stream);
     const uint64_t n = n_leaves, bytes_per_row = 8 * (uint64_t)width;
-    if (n <= kSmallTree) {
+    // below 64 MiB of rows the copy takes less than the extra launches would
+    // save: one copy, then the device-rows build
+    if (n <= kSmallTree || n * bytes_per_row < (64ull << 20)) {
         PG_CUDA(cudaMemcpyAsync(rows_dev, rows_host, n * bytes_per_row, cudaMemcpyHostToDevice, st));
         return pg_merkle_build(rows_dev, n_leaves, width, nodes, root_out, stream);
     }
