@@ -43,7 +43,7 @@ IMAD_RESULTS_PER_CLK_SM = 64  # 32-bit multiply results per clock per SM
 # current kernels on that workload (params, log2 leaves, width); other
 # workloads report null.
 KERNEL_TRAFFIC = {("pg12_v1", 22, 8, "k_merkle"): 369_402_445,
-                  ("pg12_v1", 22, 8, "k_hash_rows"): 37_468_877,
+                  ("pg12_v1", 22, 8, "k_merkle_level"): 37_468_877,
                   ("pg12_v1", 22, 8, "k_merkle_top"): 100_299}
 
 

@@ -1,9 +1,9 @@
 // Kernels and C ABI of the GB300 Poseidon-12 / Goldilocks Merkle library.
 //
 //   k_permute   Alg. 1 on a batch of independent states, one thread each.
-//   k_hash_rows Sec. 2.4 sponge (rate 8, capacity 4, overwrite mode) per row;
-//               also a whole tree level (a node is the sponge of its
-//               children's eight words).
+//   k_hash_rows Sec. 2.4 sponge (rate 8, capacity 4, overwrite mode) per row.
+//   k_merkle_level  one tree level, one thread per node (a node is the
+//               sponge of its children's eight words).
 //   k_merkle    Sec. 4.2 persistent tree kernel: warps pull 32-leaf tasks
 //               from a global counter and hash those rows; up to a plan's
 //               climb limit, the warp that completes the second of two
@@ -154,6 +154,22 @@ __global__ void __launch_bounds__(kSmallBlock) k_hash_rows(const uint64_t *__res
         sponge_slot<kSmallBlock, MDS>(rows + r * w, w, vec16 != 0, slot);
         st2(out + kDigest * r, canon(slot[0]), canon(slot[kSmallBlock]));
         st2(out + kDigest * r + 2, canon(slot[2 * kSmallBlock]), canon(slot[3 * kSmallBlock]));
+    }
+}
+
+// One tree level, one thread per node: node k is the sponge of the eight
+// words of children 2k and 2k+1 (contiguous in the level below, 16-byte
+// aligned), i.e. perm([L, R, 0^4])[0..3].
+template <int MDS>
+__global__ void __launch_bounds__(kSmallBlock) k_merkle_level(const uint64_t *__restrict__ below, uint64_t count,
+                                                              uint64_t *__restrict__ here) {
+    __shared__ uint64_t slots[kT * kSmallBlock];
+    uint64_t *slot = slots + threadIdx.x;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < count; k += stride) {
+        sponge_slot<kSmallBlock, MDS>(below + 2 * kDigest * k, 2 * kDigest, true, slot);
+        st2(here + kDigest * k, canon(slot[0]), canon(slot[kSmallBlock]));
+        st2(here + kDigest * k + 2, canon(slot[2 * kSmallBlock]), canon(slot[3 * kSmallBlock]));
     }
 }
 
@@ -465,9 +481,8 @@ constexpr size_t kWorkspaceBytes = 32u << 20;  // tree plans + arrival counters
 // kTopNodes nodes (by default only the leaves: one launch per level measured
 // faster than climbing with arrival counters, 16.7 against 17.4 ms for a
 // 2^22 x 8 tree), and every other level is one launch: one thread per node
-// (k_hash_rows over the children, since a node is the sponge of its
-// children's eight words) while the level has more than kWideNodes nodes,
-// the 16-lanes-per-state kernel above that.
+// (k_merkle_level) while the level has more than kWideNodes nodes, the
+// 16-lanes-per-state kernel above that.
 #ifndef PG12_TOP_NODES
 #define PG12_TOP_NODES (1ull << 40)
 #endif
@@ -487,7 +502,7 @@ constexpr size_t kPlanBytes = 4u << 20;        // first part: plans; rest: count
 const char *const kKernelNames[kIdCount] = {"k_merkle",      "k_merkle_top",    "k_merkle_top_leaf",
                                             "k_permute",     "k_hash_rows",     "k_merkle_open",
                                             "k_merkle_verify", "k_merkle_single", "batch_graph",
-                                            "k_ntt_pass",    "k_ntt_bitrev"};
+                                            "k_ntt_pass",    "k_ntt_bitrev",    "k_merkle_level"};
 constexpr size_t kProfMaxRecords = 1u << 16;
 
 struct ProfRecord {
@@ -625,8 +640,8 @@ pg_status plan_batch(const pg_tree *trees, size_t n_trees, const pg_schedule *sc
 }
 
 // One launch per level for levels first..log2(n_leaves) of a tree whose
-// lower levels are in `nodes`: one thread per node while a level has more
-// than kWideNodes nodes, the 16-lanes-per-state kernel above that.
+// lower levels are in `nodes`: one thread per node (k_merkle_level) while a
+// level has more than kWideNodes nodes, the 16-lanes-per-state kernel above.
 pg_status launch_levels(uint64_t *nodes, uint64_t n_leaves, uint32_t first, cudaStream_t st) {
     const uint32_t log_n = log2u(n_leaves);
     for (uint32_t l = first; l <= log_n; ++l) {
@@ -635,11 +650,11 @@ pg_status launch_levels(uint64_t *nodes, uint64_t n_leaves, uint32_t first, cuda
             const uint64_t *below = nodes + 4 * (2 * n_leaves - ((2 * n_leaves) >> (l - 1)));
             uint64_t *here = nodes + 4 * (2 * n_leaves - ((2 * n_leaves) >> l));
             const unsigned grid = (unsigned)((cnt + 127) / 128);
-            ProfScope prof(kIdHashRows, st, cnt);
+            ProfScope prof(kIdMerkleLevel, st, cnt);
             if (g.params_set == 1)
-                dev::k_hash_rows<dev::kMdsSmall><<<grid, 128, 0, st>>>(below, cnt, 8, 1, here);
+                dev::k_merkle_level<dev::kMdsSmall><<<grid, 128, 0, st>>>(below, cnt, here);
             else
-                dev::k_hash_rows<dev::kMdsFull><<<grid, 128, 0, st>>>(below, cnt, 8, 1, here);
+                dev::k_merkle_level<dev::kMdsFull><<<grid, 128, 0, st>>>(below, cnt, here);
         } else {
             const unsigned grid = (unsigned)((cnt * 16 + dev::kTopBlock - 1) / dev::kTopBlock);
             ProfScope prof(kIdMerkleTop, st, cnt);

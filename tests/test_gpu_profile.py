@@ -45,13 +45,14 @@ def test_build_launches_account_for_every_permutation(log_n, w):
     assert all(v["total_ms"] > 0 for v in got.values())
     n = 1 << log_n
     # the leaves in one launch (persistent kernel above 8,192 leaves, else the 16-lane
-    # kernel), then one launch per level: one thread per node above 8,192 nodes
+    # kernel), then one launch per level: one thread per node (k_merkle_level) above 8,192
+    # nodes, else the 16-lane kernel (k_merkle_top)
     if n > 8192:
         assert got["k_merkle"]["launches"] == 2 and got["k_merkle"]["perms"] == 2 * n * ((w + 7) // 8)
     else:
         assert "k_merkle" not in got and got["k_merkle_top_leaf"]["launches"] == 2
     per_node = sum(1 for l in range(1, log_n + 1) if n >> l > 8192)
-    assert got.get("k_hash_rows", {"launches": 0})["launches"] == 2 * per_node
+    assert got.get("k_merkle_level", {"launches": 0})["launches"] == 2 * per_node
     assert got.get("k_merkle_top", {"launches": 0})["launches"] == 2 * (log_n - per_node)
 
 
