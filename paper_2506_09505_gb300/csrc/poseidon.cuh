@@ -227,14 +227,19 @@ __device__ __forceinline__ uint64_t add_weak(uint64_t a, uint64_t b) {
 // mask; every lane of the group must execute this.  Latency is what matters
 // here, so the critical path is kept short: in a partial round the products
 // v_e x_e (e >= 1) and their butterfly sum do not wait for the S-box; only
-// v_0 x_0^7 is added after it.  Dense rows use two accumulators.
+// v_0 x_0^7 is added after it.  Dense rows use two accumulators.  There are
+// no lane-dependent branches (a divergent warp would run the two sides one
+// after the other): every lane computes and operands are selected.  Lanes 12
+// to 15 carry values nobody reads (dense rows gather lanes 0-11, x_0 comes
+// from lane 0, and their products are masked out of the sum).
 __device__ __forceinline__ uint64_t permute_wide(uint64_t x, int lane16, unsigned gmask, const DevConsts &K) {
     const int e = lane16 < kT ? lane16 : 0;
-    const bool live = lane16 < kT;
+    const uint64_t pmask = (lane16 >= 1 && lane16 < kT) ? ~0ull : 0ull;
+    const bool lane0 = lane16 == 0;
     const int base = (threadIdx.x & 31) & ~15;
 #pragma unroll 1
     for (int r = 0; r < kRF; ++r) {
-        x = live ? sbox(add_canon(x, K.full_rc[r][e])) : 0;
+        x = sbox(add_canon(x, K.full_rc[r][e]));
         const int m = r == kRF / 2 - 1 ? 1 : 0;
         Acc A, B;
         acc_zero(A);
@@ -246,18 +251,19 @@ __device__ __forceinline__ uint64_t permute_wide(uint64_t x, int lane16, unsigne
             acc_mac(A, xa, K.mat[m][e][j]);
             acc_mac(B, xb, K.mat[m][e][j + 1]);
         }
-        x = live ? add_weak(acc_reduce(A), acc_reduce(B)) : 0;
+        x = add_weak(acc_reduce(A), acc_reduce(B));
         if (r == kRF / 2 - 1) {
 #pragma unroll 1
             for (int q = 0; q < kRP; ++q) {
                 const uint64_t x0 = __shfl_sync(gmask, x, base);
                 const uint64_t y = sbox(add_canon(x0, K.part_rc[q]));
                 // sum of v_e x_e over e = 1..11 (independent of the S-box)
-                uint64_t t = (live && e != 0) ? mul(x, K.part_v[q][e]) : 0;
+                uint64_t t = mul(x, K.part_v[q][e]) & pmask;
 #pragma unroll
                 for (int d = 8; d >= 1; d >>= 1) t = add_weak(t, __shfl_xor_sync(gmask, t, d));
-                x = e == 0 ? mul_add(K.part_v[q][0], y, t)
-                           : (live ? mul_add(K.part_w[q][e], y, x) : 0);
+                // lane 0: v_0 y + t; lane e: x_e + w_e y
+                const uint64_t coef = lane0 ? K.part_v[q][0] : K.part_w[q][e];
+                x = mul_add(coef, y, lane0 ? t : x);
             }
         }
     }
