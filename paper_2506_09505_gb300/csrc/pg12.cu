@@ -329,6 +329,35 @@ __global__ void __launch_bounds__(kBlock) k_merkle_single(const TreePlan tp, uin
 // lanes 0..3 store the digest.  Every lane reaches the shuffles (groups past
 // the level's end compute on a dummy node and skip the store).
 constexpr int kTopBlock = 256;
+// The last levels of a tree (at most kTailNodes nodes each) in one block:
+// one 16-lane group per node, a block barrier between levels.  Saves a
+// launch and a constant copy per level where each level is one
+// permutation's latency anyway.
+constexpr int kTailBlock = 512;  // 32 groups; at 1024 threads the 64-register cap spills
+constexpr uint64_t kTailNodes = kTailBlock / 16;
+__global__ void __launch_bounds__(kTailBlock) k_merkle_top_tail(uint64_t *__restrict__ nodes, uint64_t n,
+                                                                uint32_t first) {
+    __shared__ __align__(16) DevConsts K;
+    load_consts(K);
+    const uint32_t log_n = 63 - __clzll(n);
+    const uint64_t gid = threadIdx.x >> 4;
+    const int l16 = threadIdx.x & 15;
+    for (uint32_t level = first; level <= log_n; ++level) {
+        const uint64_t count = n >> level;
+        // whole warps hold groups 2w and 2w + 1; a warp past the level's end skips it
+        if ((gid & ~1ull) < count) {
+            const bool valid = gid < count;
+            const uint64_t node = valid ? gid : 0;
+            const uint64_t *kids = nodes + kDigest * (level_off(n, level - 1) + 2 * node);
+            uint64_t x = 0;
+            if (l16 < 2 * kDigest) x = kids[l16];
+            x = permute_wide(x, l16, 0xFFFFFFFFu, K);
+            if (valid && l16 < kDigest) nodes[kDigest * (level_off(n, level) + node) + l16] = canon(x);
+        }
+        __syncthreads();
+    }
+}
+
 __global__ void __launch_bounds__(kTopBlock) k_merkle_top(uint64_t *__restrict__ nodes, uint64_t n, uint32_t level) {
     __shared__ __align__(16) DevConsts K;
     load_consts(K);
@@ -502,7 +531,8 @@ constexpr size_t kPlanBytes = 4u << 20;        // first part: plans; rest: count
 const char *const kKernelNames[kIdCount] = {"k_merkle",      "k_merkle_top",    "k_merkle_top_leaf",
                                             "k_permute",     "k_hash_rows",     "k_merkle_open",
                                             "k_merkle_verify", "k_merkle_single", "batch_graph",
-                                            "k_ntt_pass",    "k_ntt_bitrev",    "k_merkle_level"};
+                                            "k_ntt_pass",    "k_ntt_bitrev",    "k_merkle_level",
+                                            "k_merkle_top_tail"};
 constexpr size_t kProfMaxRecords = 1u << 16;
 
 struct ProfRecord {
@@ -646,6 +676,13 @@ pg_status launch_levels(uint64_t *nodes, uint64_t n_leaves, uint32_t first, cuda
     const uint32_t log_n = log2u(n_leaves);
     for (uint32_t l = first; l <= log_n; ++l) {
         const uint64_t cnt = n_leaves >> l;
+        if (cnt <= dev::kTailNodes && l < log_n) {
+            // this level and all above it in one block
+            ProfScope prof(kIdMerkleTopTail, st, 2 * cnt - 1);
+            dev::k_merkle_top_tail<<<1, dev::kTailBlock, 0, st>>>(nodes, n_leaves, l);
+            PG_CUDA(cudaGetLastError());
+            break;
+        }
         if (cnt > kWideNodes) {
             const uint64_t *below = nodes + 4 * (2 * n_leaves - ((2 * n_leaves) >> (l - 1)));
             uint64_t *here = nodes + 4 * (2 * n_leaves - ((2 * n_leaves) >> l));

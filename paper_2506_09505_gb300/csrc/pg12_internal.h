@@ -40,7 +40,7 @@ int set_error(int status, const char *fmt, ...);
 // on.  Defined in pg12.cu; the stream and events are held as opaque pointers.
 enum KernelId {
     kIdMerkle, kIdMerkleTop, kIdMerkleTopLeaf, kIdPermute, kIdHashRows, kIdOpen, kIdVerify, kIdSingle,
-    kIdGraph, kIdNttPass, kIdNttBitrev, kIdMerkleLevel, kIdCount
+    kIdGraph, kIdNttPass, kIdNttBitrev, kIdMerkleLevel, kIdMerkleTopTail, kIdCount
 };
 
 class ProfScope {
