@@ -108,7 +108,12 @@ enum {
     PG_OP_DOT12 = 8,     /* 12-term dot product, bench only (spmv/mmult rows)       */
     PG_OP_PIPE_IMAD = 9,       /* bench only: raw mad.lo.u32 throughput (IMAD)      */
     PG_OP_PIPE_IMAD_WIDE = 10, /* bench only: raw mad.wide.u32 throughput           */
-    PG_OP_PIPE_IADD = 11       /* bench only: raw 32-bit add throughput             */
+    PG_OP_PIPE_IADD = 11,      /* bench only: raw 32-bit add throughput             */
+    PG_OP_LAT_MUL = 12,        /* bench only: latency of a dependent chain of a * b */
+    PG_OP_LAT_SBOX = 13,       /* bench only: latency of x^7                        */
+    PG_OP_LAT_DOT12 = 14,      /* bench only: latency of a 12-term dot product      */
+    PG_OP_LAT_PERM = 15,       /* bench only: latency of one permutation, one thread per state */
+    PG_OP_LAT_PERM_WIDE = 16   /* bench only: latency of one permutation, 16 lanes per state   */
 };
 
 /* Library version, e.g. "pg12 1.0 sm_103a". */
@@ -328,8 +333,11 @@ pg_status pg_field_eval(int op, const uint64_t *a, const uint64_t *b, uint64_t *
 /*
  * pg_field_bench -- throughput of one operation on the current device
  * (twelve independent chains per thread, grid = SMs x occupancy): results
- * per second and per SM clock (clock64-timed).  Synchronous; allocates and
- * frees two small device buffers.
+ * per second and per SM clock (clock64-timed).  For the PG_OP_LAT_* ops, the
+ * latency instead: one warp runs one dependent chain of the operation;
+ * ops_per_clk_sm receives the SM cycles per operation and ops_per_s the
+ * operations per second of that chain.  Synchronous; allocates and frees two
+ * small device buffers.
  */
 pg_status pg_field_bench(int op, double *ops_per_s, double *ops_per_clk_sm);
 

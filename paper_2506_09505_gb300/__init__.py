@@ -126,7 +126,8 @@ SIGNATURES = {
 }
 
 OPS = {"add": 1, "sub": 2, "mul": 3, "sqr": 4, "reduce": 5, "mul_small": 6, "sbox": 7, "dot12": 8,
-       "pipe_imad": 9, "pipe_imad_wide": 10, "pipe_iadd": 11}
+       "pipe_imad": 9, "pipe_imad_wide": 10, "pipe_iadd": 11,
+       "lat_mul": 12, "lat_sbox": 13, "lat_dot12": 14, "lat_perm": 15, "lat_perm_wide": 16}
 
 
 def lib_path() -> str:
@@ -411,7 +412,8 @@ def field_eval(op: str, a, b=None, stream=None):
 
 
 def field_bench(op: str):
-    """(results per second, results per SM clock) of one field operation."""
+    """(results per second, results per SM clock) of one field operation; for the
+    ``lat_*`` ops, (operations per second of one dependent chain, cycles per operation)."""
     rate, per_clk = ctypes.c_double(), ctypes.c_double()
     _check(load().pg_field_bench(OPS[op], ctypes.byref(rate), ctypes.byref(per_clk)))
     return rate.value, per_clk.value

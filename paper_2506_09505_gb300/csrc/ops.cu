@@ -6,6 +6,7 @@
 #include "pg12.h"
 #include "pg12_internal.h"
 #include "field.cuh"
+#include "poseidon.cuh"
 
 #include <cuda_runtime.h>
 
@@ -119,14 +120,84 @@ __global__ void __launch_bounds__(256) k_pipe_bench(uint64_t *out, long long *cy
     if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
 }
 
+
+// Latency chains: one warp, each operation consumes the previous result.
+// The constant tables are arbitrary words (latency does not depend on them).
+template <int OP>
+__global__ void k_lat_bench(uint64_t *out, long long *cycles, int iters) {
+    __shared__ __align__(16) DevConsts K;
+    __shared__ uint64_t slots[kT * 32];
+    uint64_t *w = reinterpret_cast<uint64_t *>(&K);
+    for (unsigned i = threadIdx.x; i < sizeof(DevConsts) / 8; i += blockDim.x) w[i] = 0x9E3779B97F4A7C15ull * (i + 1);
+    uint64_t *slot = slots + threadIdx.x;
+    for (int i = 0; i < kT; ++i) slot[i * 32] = 0x100000001ull * (threadIdx.x + 7 * i + 1);
+    __syncthreads();
+    uint64_t x = 0x9E3779B97F4A7C15ull + threadIdx.x;
+    const uint64_t y = 0x123456789ABCDEFull;
+    const long long t0 = clock64();
+    for (int it = 0; it < iters; ++it) {
+        if (OP == PG_OP_LAT_MUL) {
+            x = mul(x, y);
+        } else if (OP == PG_OP_LAT_SBOX) {
+            x = sbox(x);
+        } else if (OP == PG_OP_LAT_DOT12) {
+            Acc A;
+            acc_zero(A);
+#pragma unroll
+            for (int j = 0; j < kT; ++j) acc_mac(A, x + j, y + 977 * j);
+            x = acc_reduce(A);
+        } else if (OP == PG_OP_LAT_PERM) {
+            slot[0] += x;
+            permute_slot<32>(slot);
+            x = slot[0];
+        } else {
+            x = permute_wide(x, threadIdx.x & 15, 0xFFFFFFFFu, K);
+        }
+    }
+    const long long t1 = clock64();
+    if (threadIdx.x == 0) cycles[0] = t1 - t0;
+    out[threadIdx.x] = x;
+}
+
 }  // namespace dev
 }  // namespace pg12
 
 using namespace pg12;
 
 namespace {
+
+
 pg_status ops_fail(pg_status s, const char *what, cudaError_t e) {
     return (pg_status)set_error(s, "%s: %s", what, cudaGetErrorString(e));
+}
+
+template <int OP>
+pg_status lat_one(int sms, double *ops_per_s, double *ops_per_clk_sm) {
+    (void)sms;
+    const int iters = OP == PG_OP_LAT_PERM || OP == PG_OP_LAT_PERM_WIDE ? 16 : 1024;
+    uint64_t *out = nullptr;
+    long long *cyc = nullptr;
+    cudaError_t e;
+    if ((e = cudaMalloc(&out, sizeof(uint64_t) * 32)) != cudaSuccess) return ops_fail(PG_ERR_OOM, "malloc", e);
+    if ((e = cudaMalloc(&cyc, sizeof(long long))) != cudaSuccess) {
+        cudaFree(out);
+        return ops_fail(PG_ERR_OOM, "malloc", e);
+    }
+    dev::k_lat_bench<OP><<<1, 32>>>(out, cyc, 2);
+    dev::k_lat_bench<OP><<<1, 32>>>(out, cyc, iters);
+    e = cudaDeviceSynchronize();
+    long long h = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&h, cyc, sizeof h, cudaMemcpyDeviceToHost);
+    int dev_id = 0, khz = 0;
+    cudaGetDevice(&dev_id);
+    cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev_id);
+    cudaFree(out);
+    cudaFree(cyc);
+    if (e != cudaSuccess) return ops_fail(PG_ERR_CUDA, "latency kernel", e);
+    const double per_op = (double)h / iters;
+    if (ops_per_clk_sm) *ops_per_clk_sm = per_op;
+    if (ops_per_s) *ops_per_s = per_op > 0 ? (double)khz * 1e3 / per_op : 0.0;
+    return PG_OK;
 }
 
 template <int KIND>
@@ -236,6 +307,11 @@ pg_status pg_field_bench(int op, double *ops_per_s, double *ops_per_clk_sm) {
         case PG_OP_PIPE_IMAD: return pipe_one<0>(sms, ops_per_s, ops_per_clk_sm);
         case PG_OP_PIPE_IMAD_WIDE: return pipe_one<1>(sms, ops_per_s, ops_per_clk_sm);
         case PG_OP_PIPE_IADD: return pipe_one<2>(sms, ops_per_s, ops_per_clk_sm);
+        case PG_OP_LAT_MUL: return lat_one<PG_OP_LAT_MUL>(sms, ops_per_s, ops_per_clk_sm);
+        case PG_OP_LAT_SBOX: return lat_one<PG_OP_LAT_SBOX>(sms, ops_per_s, ops_per_clk_sm);
+        case PG_OP_LAT_DOT12: return lat_one<PG_OP_LAT_DOT12>(sms, ops_per_s, ops_per_clk_sm);
+        case PG_OP_LAT_PERM: return lat_one<PG_OP_LAT_PERM>(sms, ops_per_s, ops_per_clk_sm);
+        case PG_OP_LAT_PERM_WIDE: return lat_one<PG_OP_LAT_PERM_WIDE>(sms, ops_per_s, ops_per_clk_sm);
         default: return (pg_status)set_error(PG_ERR_INVALID_ARG, "unknown op %d", op);
     }
 }

@@ -64,3 +64,13 @@ def test_field_mul_matches_oracle():
 def test_field_bench_runs(op):
     rate, per_clk = pg.field_bench(op)
     assert rate > 0 and per_clk > 0
+
+
+def test_latency_chains_are_ordered():
+    # one dependent chain per op: an S-box is at least three products deep, a permutation
+    # (8 full + 22 partial rounds, 30 S-boxes in sequence) far deeper than one S-box
+    lat = {op: pg.field_bench(op)[1] for op in ("lat_mul", "lat_sbox", "lat_dot12", "lat_perm", "lat_perm_wide")}
+    assert all(v > 0 for v in lat.values())
+    assert lat["lat_sbox"] > 2.5 * lat["lat_mul"]
+    assert lat["lat_perm_wide"] > 20 * lat["lat_sbox"]
+    assert lat["lat_perm"] > lat["lat_perm_wide"]
