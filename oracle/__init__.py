@@ -54,6 +54,7 @@ def _load():
         "orc_mul": (u64, [u64, u64]),
         "orc_pow": (u64, [u64, u64]),
         "orc_inv": (u64, [u64]),
+        "orc_field_many": (i, [i, _u64p, _u64p, _u64p, sz]),
         "orc_sbox_inverse_exponent": (u64, []),
         "orc_mat_inverse": (i, [_u64p, _u64p, i]),
         "orc_mat_det": (u64, [_u64p, i]),
@@ -108,6 +109,20 @@ def sub(a: int, b: int) -> int:
 
 def mul(a: int, b: int) -> int:
     return int(_load().orc_mul(a, b))
+
+
+FIELD_MANY_OPS = {"add": 1, "sub": 2, "mul": 3, "sqr": 4, "sbox": 5}
+
+
+def field_many(op: str, a, b=None) -> np.ndarray:
+    """Element-wise add / sub / mul / sqr / sbox (x^7) over arrays of words, canonical (Eq. 1)."""
+    a = _u64(a)
+    b = _u64(b) if b is not None else a
+    assert a.shape == b.shape
+    out = np.empty_like(a)
+    if _load().orc_field_many(FIELD_MANY_OPS[op], _ptr(a), _ptr(b), _ptr(out), a.size) != 0:
+        raise ValueError(op)
+    return out
 
 
 def pow_(a: int, e: int) -> int:

@@ -79,6 +79,21 @@ uint64_t orc_inv(uint64_t a) { return orc_pow(a, ORC_P - 2); }
 /* S-box of Alg. 1: x^7. */
 static uint64_t orc_sbox(uint64_t x) { return orc_pow(x, 7); }
 
+/* Element-wise field operation over n pairs (Eq. 1), canonical results:
+ * op 1 a+b, 2 a-b, 3 a*b, 4 a^2, 5 a^7.  b is ignored for ops 4 and 5.
+ * Returns 0, or -1 for an unknown op. */
+int orc_field_many(int op, const uint64_t *a, const uint64_t *b, uint64_t *out, size_t n) {
+    size_t i;
+    switch (op) {
+    case 1: for (i = 0; i < n; ++i) out[i] = orc_add(a[i], b[i]); return 0;
+    case 2: for (i = 0; i < n; ++i) out[i] = orc_sub(a[i], b[i]); return 0;
+    case 3: for (i = 0; i < n; ++i) out[i] = orc_mul(a[i], b[i]); return 0;
+    case 4: for (i = 0; i < n; ++i) out[i] = orc_mul(a[i], a[i]); return 0;
+    case 5: for (i = 0; i < n; ++i) out[i] = orc_sbox(a[i]); return 0;
+    default: return -1;
+    }
+}
+
 /* d with 7*d = 1 mod (p-1), so (x^7)^d = x: extended Euclid on (7, p-1). */
 uint64_t orc_sbox_inverse_exponent(void) {
     __int128 r0 = (__int128)(ORC_P - 1), r1 = 7, s0 = 0, s1 = 1;

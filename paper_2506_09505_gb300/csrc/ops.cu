@@ -53,6 +53,21 @@ __global__ void k_field_eval(int op, const uint64_t *__restrict__ a, const uint6
         out[i] = canon(apply(op, a[i], b ? b[i] : 0));
 }
 
+// Arbitrary distinct matrix entries for the dot-product benchmark (a
+// SplitMix64 finaliser of the position, reduced below p).  Both 32-bit halves
+// differ from entry to entry, so the compiler cannot share a partial product
+// between rows.
+__host__ __device__ constexpr uint64_t bench_entry(int i, int j) {
+    uint64_t z = 0x9E3779B97F4A7C15ull * (uint64_t)(i * 12 + j + 1);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return (z ^ (z >> 31)) % P;
+}
+
+// The benchmark matrix, filled by the host before a dot-product run (the
+// permutation also reads its matrices from the constant bank).
+__constant__ uint64_t c_bench_m[12][12];
+
 // Twelve independent chains per thread; clock64 brackets the timed loop.
 template <int OP>
 __global__ void __launch_bounds__(256) k_field_bench(uint64_t *out, long long *cycles, int iters) {
@@ -66,12 +81,11 @@ __global__ void __launch_bounds__(256) k_field_bench(uint64_t *out, long long *c
 #pragma unroll
         for (int i = 0; i < 12; ++i) {
             if (OP == PG_OP_DOT12) {
-                // one 12-term lazy dot product per step, writing back to cell i;
-                // every row has its own constants (no product repeats across rows)
+                // one 12-term lazy dot product per step, writing back to cell i
                 Acc A;
                 acc_zero(A);
 #pragma unroll
-                for (int j = 0; j < 12; ++j) acc_mac(A, x[j], c + 977ull * j + 0x10001ull * i);
+                for (int j = 0; j < 12; ++j) acc_mac(A, x[j], c_bench_m[i][j]);
                 x[i] = acc_reduce(A);
             } else {
                 x[i] = apply(OP, x[i], x[(i + 1) % 12] ^ c);
@@ -244,6 +258,13 @@ pg_status bench_one(int sms, double *ops_per_s, double *ops_per_clk_sm) {
     if (e != cudaSuccess || occ < 1) return ops_fail(PG_ERR_CUDA, "occupancy", e);
     const int grid = sms * occ, threads = 256;
     const int iters = OP == PG_OP_DOT12 ? 20 : (OP == PG_OP_SBOX ? 50 : 200);
+    if (OP == PG_OP_DOT12) {
+        uint64_t m[12][12];
+        for (int i = 0; i < 12; ++i)
+            for (int j = 0; j < 12; ++j) m[i][j] = dev::bench_entry(i, j);
+        if ((e = cudaMemcpyToSymbol(dev::c_bench_m, m, sizeof(m))) != cudaSuccess)
+            return ops_fail(PG_ERR_CUDA, "bench constants", e);
+    }
     uint64_t *out = nullptr;
     long long *cyc = nullptr;
     if ((e = cudaMalloc(&out, sizeof(uint64_t) * grid * threads)) != cudaSuccess) return ops_fail(PG_ERR_OOM, "malloc", e);

@@ -74,3 +74,19 @@ def test_latency_chains_are_ordered():
     assert lat["lat_sbox"] > 2.5 * lat["lat_mul"]
     assert lat["lat_perm_wide"] > 20 * lat["lat_sbox"]
     assert lat["lat_perm"] > lat["lat_perm_wide"]
+
+
+@pytest.fixture(scope="module")
+def big_pairs():
+    # 10^8 full-range words per operand (weak, non-canonical inputs included)
+    n = 10 ** 8
+    return pg_synth.words(0xF10, n, bound=None), pg_synth.words(0xF11, n, bound=None)
+
+
+@pytest.mark.parametrize("op", ["add", "sub", "mul", "sqr", "sbox"])
+def test_field_op_1e8_random_pairs_vs_oracle(big_pairs, op):
+    a, b = big_pairs
+    got = _run(op, a, b)
+    want = oracle.field_many(op, a, b)
+    bad = np.flatnonzero(got != want)
+    assert bad.size == 0, (op, bad[:5], a[bad[:5]], b[bad[:5]])

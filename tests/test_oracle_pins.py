@@ -48,6 +48,22 @@ def test_field_ops_random_vs_bigint():
         assert oracle.sub(a, b) == (a - b) % P
 
 
+@pytest.mark.parametrize("op,fn", [
+    ("add", lambda a, b: (a + b) % P),
+    ("sub", lambda a, b: (a - b) % P),
+    ("mul", lambda a, b: (a * b) % P),
+    ("sqr", lambda a, b: (a * a) % P),
+    ("sbox", lambda a, b: pow(a, 7, P)),
+])
+def test_field_many_vs_bigint(op, fn):
+    # the element-wise entry point that the GPU field tests compare against
+    e = np.array(EDGE, dtype=np.uint64)
+    a = np.concatenate([np.repeat(e, len(e)), pg_synth.words(0xA11, 4000, bound=None)])
+    b = np.concatenate([np.tile(e, len(e)), pg_synth.words(0xA12, 4000, bound=None)])
+    got = oracle.field_many(op, a, b)
+    assert [int(v) for v in got] == [fn(int(x), int(y)) for x, y in zip(a, b)]
+
+
 def test_limb_identities():
     # the special-prime identities behind Alg. 2 / Eqs. 2-4
     assert oracle.pow_(2, 64) == EPS
