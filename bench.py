@@ -42,9 +42,10 @@ IMAD_RESULTS_PER_CLK_SM = 64  # 32-bit multiply results per clock per SM
 # kernel of a tree build, averaged over its launches in one ncu capture of the
 # current kernels on that workload (params, log2 leaves, width); other
 # workloads report null.
-KERNEL_TRAFFIC = {("pg12_v1", 22, 8, "k_merkle"): 369_402_445,
-                  ("pg12_v1", 22, 8, "k_merkle_level"): 37_468_877,
-                  ("pg12_v1", 22, 8, "k_merkle_top"): 100_299}
+KERNEL_TRAFFIC = {("pg12_v1", 22, 8, "k_merkle"): 369_620_121,
+                  ("pg12_v1", 22, 8, "k_merkle_level"): 37_438_291,
+                  ("pg12_v1", 22, 8, "k_merkle_top"): 155_139,
+                  ("pg12_v1", 22, 8, "k_merkle_top_tail"): 41_344}
 
 
 def algorithmic_bytes(kernel, perms_per_launch, width):
@@ -648,7 +649,7 @@ def run_lde(args):
     kern.pop("_dropped", None)
     ms = e0.elapsed_time(e1) / args.steps
     lde_ms = kern["k_ntt_pass"]["total_ms"] / args.steps
-    # one product per butterfly (8 results) and three per coefficient for the coset factor
+    # one product per butterfly (8 results) and four per input coefficient for the coset factor
     butterflies = (n // 2) * log_n * cols + (big // 2) * log_n * cols
     mul_results = 8 * (butterflies + 4 * n * cols)
     alg_bytes = 8 * cols * (n + big)
