@@ -2,10 +2,12 @@
 """Benchmark of the Poseidon-12 / Goldilocks Merkle build on GB300.
 
 One step = one whole Merkle tree (Sec. 4.2) over 2^22 synthetic leaf rows of
-8 Goldilocks words: leaf sponge hashing, then every level up to the root --
-8,388,607 permutations, all in one persistent kernel launch.  The rows
-(256 MiB) stay resident in HBM; they are larger than the 129 MB L2, so no
-flush is needed between steps.
+8 Goldilocks words: leaf sponge hashing in one persistent launch, then every
+level up to the root (one launch per level of more than 64 nodes, one cluster
+launch for the rest) -- 8,388,607 permutations.  The rows (256 MiB) stay
+resident in HBM; they are larger than the 129 MB L2, so no flush is needed
+between steps (smaller trees, --log-n, get a 512 MiB write between steps,
+outside the timed brackets).
 
 Printed (rank 0, one JSON line): throughput in permutations/s over the
 whole job, the build time in ms, the roofline of the kernel against the
@@ -38,6 +40,7 @@ MUL_RESULTS_PER_PERM = 118 * (2 * 6 + 2 * 8) + 8 * 144 * 8 + 22 * 23 * 8
 # IMAD.WIDE per term (4 results); round 3's transition matrix stays full width.
 MUL_RESULTS_PER_PERM_SMALL = 118 * (2 * 6 + 2 * 8) + 7 * 144 * 4 + 144 * 8 + 22 * 23 * 8
 IMAD_RESULTS_PER_CLK_SM = 64  # 32-bit multiply results per clock per SM
+L2_BYTES = 129 * 10**6  # GB300 L2
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of each
 # kernel of a tree build, averaged over its launches in one ncu capture of the
 # current kernels on that workload (params, log2 leaves, width); other
@@ -300,22 +303,40 @@ def run_ours(args):
         gpu_id = "GPU-" + str(props.uuid) if not str(props.uuid).startswith("GPU-") else str(props.uuid)
     except Exception:
         gpu_id = None
+    # Rows smaller than twice the L2 would stay cached from one step to the
+    # next: then a 512 MiB write evicts them between steps, outside the timed
+    # step brackets.
+    flush = rows_np.nbytes < 2 * L2_BYTES
+    scratch = torch.empty(512 << 20, dtype=torch.uint8, device="cuda") if flush else None
+
+    def timed_steps(kernel_events):
+        """Per-step device times (ms) of args.steps builds; with kernel_events the
+        library also brackets each of its launches with CUDA events."""
+        ea = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        eb = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        pg.profile_enable(kernel_events)
+        for k in range(args.steps):
+            if flush:
+                scratch.zero_()
+            ea[k].record(stream)
+            pg.merkle_build(rows, nodes)
+            eb[k].record(stream)
+        barrier()
+        kern = pg.profile_read() if kernel_events else None
+        pg.profile_enable(False)
+        return [a.elapsed_time(b) for a, b in zip(ea, eb)], kern
+
     barrier()
     sampler = ClockSampler(gpu_id)
     time.sleep(0.4)
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
-    # per-kernel CUDA events, recorded by the library on the launching stream
-    pg.profile_enable(True)
-    ev[0].record(stream)
-    for k in range(args.steps):
-        pg.merkle_build(rows, nodes)
-        ev[k + 1].record(stream)
-    barrier()
-    kernels = pg.profile_read()
-    pg.profile_enable(False)
+    # the timed region: per-kernel CUDA events recorded by the library on the
+    # launching stream give the roofline's launch durations
+    step_ms, kernels = timed_steps(True)
     clocks = sampler.stop()
-    step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
-    total_ms = ev[0].elapsed_time(ev[-1])
+    # the same steps without the per-launch events (they cost a little per
+    # launch and keep consecutive launches from overlapping)
+    plain_ms, _ = timed_steps(False)
+    total_ms = sum(step_ms)
     if dist is not None:
         t = torch.tensor([total_ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -390,9 +411,12 @@ def run_ours(args):
         "dtype": "u64", "data": "synthetic",
         "config": {"workload": name, "leaves": n, "width": args.width, "perms_per_tree": perms,
                    "trees_per_gpu": 1, "parallelism": f"replicas x{world} (independent trees)",
-                   "l2": "inputs larger than L2 (rows 256 MiB/step at width 8), no flush",
+                   "l2": (f"rows {rows_np.nbytes / 2**20:.3g} MiB/step, under twice the L2: 512 MiB write "
+                          "between steps, outside the timed brackets" if flush else
+                          f"inputs larger than L2 (rows {rows_np.nbytes / 2**20:.3g} MiB/step), no flush"),
                    "params": args.params or "pg12_v1"},
         "build_ms": ms, "build_ms_min": min(step_ms),
+        "ms_per_step_without_kernel_events": sum(plain_ms) / len(plain_ms),
         "roofline": roofline, "e2e": e2e,
         "gpu_launches": sum(v["launches"] for v in kernels.values()) + dropped,
         "kernels": {k: {"launches": v["launches"], "ms_per_launch": v["total_ms"] / v["launches"],

@@ -227,9 +227,12 @@ pg_status pg_hash_rows(const uint64_t *rows, size_t n_rows, size_t width, uint64
  *             of nodes 2k and 2k+1 of level l-1.
  *   root_out  host, 4 words, or NULL.  When non-NULL the call synchronises
  *             `stream` and copies the root there.
- * Launches: the leaf sponges in the persistent kernel, then one launch per
- * level (trees of at most 8,192 leaves: one launch for the leaves and one per
- * level, all in the 16-lanes-per-state form).
+ * Launches: the leaf sponges in the persistent kernel (trees of at most
+ * 8,192 leaves: in the 16-lanes-per-state form), then one launch per level
+ * of more than 64 nodes and one launch of an 8-block cluster for all levels
+ * of at most 64 nodes up to the root.  Level launches use programmatic
+ * dependent launch: each may be scheduled while the previous one finishes,
+ * and reads its input only once that one has completed.
  * Uses the library workspace (allocated in pg_init) for its task counter;
  * concurrent builds on different streams are not supported.
  */

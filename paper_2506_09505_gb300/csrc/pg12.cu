@@ -114,6 +114,16 @@ __device__ __forceinline__ void sponge_slot(const uint64_t *row, uint64_t w, boo
 // ------------------------------------------------------------- kernels
 constexpr int kSmallBlock = 128;
 
+// Programmatic dependent launch.  The level kernels of a tree are launched
+// with programmatic stream serialisation: each may be scheduled while the
+// kernel before it is still running, once every block of that kernel has
+// executed pdl_trigger().  Until pdl_wait() returns it only copies the
+// constant tables (never written during a build); pdl_wait() returns when
+// the kernel before it has completed and its stores are visible.  For a
+// kernel launched without the attribute both are no-ops.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 template <int MDS>
 __global__ void __launch_bounds__(kSmallBlock) k_permute(uint64_t *__restrict__ st, uint64_t n, int vec16) {
     __shared__ uint64_t slots[kT * kSmallBlock];
@@ -149,6 +159,7 @@ __global__ void __launch_bounds__(kSmallBlock) k_hash_rows(const uint64_t *__res
                                                            uint64_t w, int vec16, uint64_t *__restrict__ out) {
     __shared__ uint64_t slots[kT * kSmallBlock];
     uint64_t *slot = slots + threadIdx.x;
+    pdl_trigger();
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
         sponge_slot<kSmallBlock, MDS>(rows + r * w, w, vec16 != 0, slot);
@@ -165,6 +176,8 @@ __global__ void __launch_bounds__(kSmallBlock) k_merkle_level(const uint64_t *__
                                                               uint64_t *__restrict__ here) {
     __shared__ uint64_t slots[kT * kSmallBlock];
     uint64_t *slot = slots + threadIdx.x;
+    pdl_trigger();
+    pdl_wait();
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < count; k += stride) {
         sponge_slot<kSmallBlock, MDS>(below + 2 * kDigest * k, 2 * kDigest, true, slot);
@@ -239,6 +252,7 @@ __global__ void __launch_bounds__(S, PG12_MERKLE_MIN_BLOCKS * 256 / S) k_merkle(
     uint64_t *slot = slots + threadIdx.x;
     const int lane = threadIdx.x & 31;
     const unsigned full = 0xFFFFFFFFu;
+    pdl_trigger();
     for (;;) {
         uint32_t task = 0;
         if (lane == 0) task = atomicAdd(next_task, 1u);
@@ -329,18 +343,26 @@ __global__ void __launch_bounds__(kBlock) k_merkle_single(const TreePlan tp, uin
 // lanes 0..3 store the digest.  Every lane reaches the shuffles (groups past
 // the level's end compute on a dummy node and skip the store).
 constexpr int kTopBlock = 256;
-// The last levels of a tree (at most kTailNodes nodes each) in one block:
-// one 16-lane group per node, a block barrier between levels.  Saves a
-// launch and a constant copy per level where each level is one
-// permutation's latency anyway.
-constexpr int kTailBlock = 512;  // 32 groups; at 1024 threads the 64-register cap spills
-constexpr uint64_t kTailNodes = kTailBlock / 16;
-__global__ void __launch_bounds__(kTailBlock) k_merkle_top_tail(uint64_t *__restrict__ nodes, uint64_t n,
-                                                                uint32_t first) {
+// The last levels of a tree (at most kTailNodes nodes each) in one launch of
+// one thread-block cluster: kTailCtas blocks on as many SMs, one 16-lane
+// group per node, a cluster barrier between levels.  Saves a launch and a
+// constant copy per level where each level is one permutation's latency
+// anyway; spread over eight SMs (one warp per scheduler at the widest level)
+// the permutations do not queue for issue slots as they do in one block.
+// Children are read with ld.global.cg (from L2): a line of a small level can
+// sit in an SM's L1 from an earlier level's read before another block of the
+// cluster has written it.
+constexpr int kTailCtas = 8;
+constexpr int kTailBlock = 128;
+constexpr uint64_t kTailNodes = kTailCtas * kTailBlock / 16;
+__global__ void __cluster_dims__(kTailCtas, 1, 1) __launch_bounds__(kTailBlock)
+    k_merkle_top_tail(uint64_t *__restrict__ nodes, uint64_t n, uint32_t first) {
     __shared__ __align__(16) DevConsts K;
     load_consts(K);
+    pdl_trigger();
+    pdl_wait();
     const uint32_t log_n = 63 - __clzll(n);
-    const uint64_t gid = threadIdx.x >> 4;
+    const uint64_t gid = ((uint64_t)blockIdx.x * kTailBlock + threadIdx.x) >> 4;
     const int l16 = threadIdx.x & 15;
     for (uint32_t level = first; level <= log_n; ++level) {
         const uint64_t count = n >> level;
@@ -350,17 +372,24 @@ __global__ void __launch_bounds__(kTailBlock) k_merkle_top_tail(uint64_t *__rest
             const uint64_t node = valid ? gid : 0;
             const uint64_t *kids = nodes + kDigest * (level_off(n, level - 1) + 2 * node);
             uint64_t x = 0;
-            if (l16 < 2 * kDigest) x = kids[l16];
+            if (l16 < 2 * kDigest) {
+                asm volatile("ld.global.cg.u64 %0, [%1];" : "=l"(x) : "l"(kids + l16));
+            }
             x = permute_wide(x, l16, 0xFFFFFFFFu, K);
             if (valid && l16 < kDigest) nodes[kDigest * (level_off(n, level) + node) + l16] = canon(x);
         }
-        __syncthreads();
+        // every thread of the cluster arrives: stores above are released to, and
+        // the next level's loads acquire from, the whole cluster
+        asm volatile("barrier.cluster.arrive.release.aligned;\n\t"
+                     "barrier.cluster.wait.acquire.aligned;" ::: "memory");
     }
 }
 
 __global__ void __launch_bounds__(kTopBlock) k_merkle_top(uint64_t *__restrict__ nodes, uint64_t n, uint32_t level) {
     __shared__ __align__(16) DevConsts K;
     load_consts(K);
+    pdl_trigger();
+    pdl_wait();
     const uint64_t count = n >> level;
     const uint64_t gid = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 4;
     const int l16 = threadIdx.x & 15;
@@ -381,6 +410,7 @@ __global__ void __launch_bounds__(kTopBlock) k_merkle_top_leaf(const uint64_t *_
                                                                uint64_t w, uint64_t *__restrict__ nodes) {
     __shared__ __align__(16) DevConsts K;
     load_consts(K);
+    pdl_trigger();
     const uint64_t gid = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 4;
     const int l16 = threadIdx.x & 15;
     const bool valid = gid < n;
@@ -672,15 +702,32 @@ pg_status plan_batch(const pg_tree *trees, size_t n_trees, const pg_schedule *sc
 // One launch per level for levels first..log2(n_leaves) of a tree whose
 // lower levels are in `nodes`: one thread per node (k_merkle_level) while a
 // level has more than kWideNodes nodes, the 16-lanes-per-state kernel above.
+// Launch a level kernel with programmatic stream serialisation (see
+// pdl_trigger / pdl_wait): it may start, and copy its constants, while the
+// kernel before it on `st` finishes.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_dependent(void (*kernel)(KArgs...), unsigned grid, unsigned block, cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 pg_status launch_levels(uint64_t *nodes, uint64_t n_leaves, uint32_t first, cudaStream_t st) {
     const uint32_t log_n = log2u(n_leaves);
     for (uint32_t l = first; l <= log_n; ++l) {
         const uint64_t cnt = n_leaves >> l;
         if (cnt <= dev::kTailNodes && l < log_n) {
-            // this level and all above it in one block
+            // this level and all above it in one cluster
             ProfScope prof(kIdMerkleTopTail, st, 2 * cnt - 1);
-            dev::k_merkle_top_tail<<<1, dev::kTailBlock, 0, st>>>(nodes, n_leaves, l);
-            PG_CUDA(cudaGetLastError());
+            PG_CUDA(launch_dependent(dev::k_merkle_top_tail, dev::kTailCtas, dev::kTailBlock, st, nodes, n_leaves, l));
             break;
         }
         if (cnt > kWideNodes) {
@@ -689,15 +736,14 @@ pg_status launch_levels(uint64_t *nodes, uint64_t n_leaves, uint32_t first, cuda
             const unsigned grid = (unsigned)((cnt + 127) / 128);
             ProfScope prof(kIdMerkleLevel, st, cnt);
             if (g.params_set == 1)
-                dev::k_merkle_level<dev::kMdsSmall><<<grid, 128, 0, st>>>(below, cnt, here);
+                PG_CUDA(launch_dependent(dev::k_merkle_level<dev::kMdsSmall>, grid, 128, st, below, cnt, here));
             else
-                dev::k_merkle_level<dev::kMdsFull><<<grid, 128, 0, st>>>(below, cnt, here);
+                PG_CUDA(launch_dependent(dev::k_merkle_level<dev::kMdsFull>, grid, 128, st, below, cnt, here));
         } else {
             const unsigned grid = (unsigned)((cnt * 16 + dev::kTopBlock - 1) / dev::kTopBlock);
             ProfScope prof(kIdMerkleTop, st, cnt);
-            dev::k_merkle_top<<<grid, dev::kTopBlock, 0, st>>>(nodes, n_leaves, l);
+            PG_CUDA(launch_dependent(dev::k_merkle_top, grid, dev::kTopBlock, st, nodes, n_leaves, l));
         }
-        PG_CUDA(cudaGetLastError());
     }
     return PG_OK;
 }

@@ -53,10 +53,10 @@ def test_build_launches_account_for_every_permutation(log_n, w):
         assert "k_merkle" not in got and got["k_merkle_top_leaf"]["launches"] == 2
     per_node = sum(1 for l in range(1, log_n + 1) if n >> l > 8192)
     assert got.get("k_merkle_level", {"launches": 0})["launches"] == 2 * per_node
-    # levels of 33..8,192 nodes: one k_merkle_top launch each; from the first level of at most
-    # 32 nodes up to the root: one k_merkle_top_tail launch (or a lone root: k_merkle_top)
-    mid = sum(1 for l in range(1, log_n + 1) if 32 < n >> l <= 8192)
-    tail_first = next((l for l in range(1, log_n + 1) if n >> l <= 32), None)
+    # levels of 65..8,192 nodes: one k_merkle_top launch each; from the first level of at most
+    # 64 nodes up to the root: one k_merkle_top_tail launch (or a lone root: k_merkle_top)
+    mid = sum(1 for l in range(1, log_n + 1) if 64 < n >> l <= 8192)
+    tail_first = next((l for l in range(1, log_n + 1) if n >> l <= 64), None)
     if tail_first is not None and tail_first < log_n:
         assert got.get("k_merkle_top_tail", {"launches": 0})["launches"] == 2
         assert got.get("k_merkle_top", {"launches": 0})["launches"] == 2 * mid
