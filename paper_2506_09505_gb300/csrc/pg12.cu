@@ -13,7 +13,12 @@
 //               climb to every tree's root.
 //   k_merkle_top / k_merkle_top_leaf
 //               the levels with few nodes, 16 lanes per state (latency form).
+//   k_merkle_top_tail
+//               every level of at most 64 nodes up to the root in one launch
+//               of an 8-block cluster, a cluster barrier between levels.
 //   k_merkle_open / k_merkle_verify  authentication paths (Sec. 2.4).
+// The level launches of a single-tree build use programmatic dependent
+// launch (pdl_trigger / pdl_wait below).
 #include "pg12.h"
 #include "pg12_internal.h"
 #include "poseidon.cuh"

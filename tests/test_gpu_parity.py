@@ -135,7 +135,7 @@ def test_merkle_workload1_all_levels_and_golden_root():
     assert root == golden
 
 
-@pytest.mark.parametrize("log_n", [0, 1, 2, 3, 5, 7, 8, 9, 10, 12, 13, 14])
+@pytest.mark.parametrize("log_n", [0, 1, 2, 3, 5, 6, 7, 8, 9, 10, 12, 13, 14, 15, 16])
 @pytest.mark.parametrize("w", [8, 5, 16])
 def test_merkle_sizes_full_compare(log_n, w):
     n = 1 << log_n
@@ -177,6 +177,25 @@ def test_merkle_rejects_non_power_of_two():
     with pytest.raises(pg.PGError) as e:
         pg.merkle_build(t, nodes=torch.zeros((5, 4), dtype=torch.int64, device="cuda"))
     assert e.value.status == 2
+
+
+@pytest.mark.parametrize("log_n", [7, 12, 17])
+def test_merkle_back_to_back_builds(log_n):
+    # consecutive builds queued on one stream with no synchronisation between
+    # them (each level launch may start while the one before finishes): every
+    # tree must still equal its oracle build
+    n = 1 << log_n
+    sets = [pg_synth.matrix(0x900 + 11 * log_n + k, n, 8) for k in range(6)]
+    devs = [dev(r) for r in sets]
+    outs = [torch.empty((2 * n - 1, 4), dtype=torch.int64, device="cuda") for _ in sets]
+    torch.cuda.synchronize()
+    for t, o in zip(devs, outs):
+        pg.merkle_build(t, o)
+    # the same buffers again, in reverse order, over the first results
+    for t, o in zip(reversed(devs), outs):
+        pg.merkle_build(t, o)
+    for r, o in zip(reversed(sets), outs):
+        assert (host(o) == oracle.merkle_build(r, nthreads=8)).all()
 
 
 def test_merkle_on_side_stream():
