@@ -25,7 +25,7 @@ OBJDIR = os.path.join(HERE, "_build")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
-# extra nvcc flags for tuning builds, e.g. PG12_NVCC_FLAGS="-DPG12_MERKLE_MIN_BLOCKS=4"
+# extra nvcc flags for tuning builds, e.g. PG12_NVCC_FLAGS="-DPG12_MERKLE_MIN_BLOCKS=3"
 EXTRA = os.environ.get("PG12_NVCC_FLAGS", "").split()
 SOURCES = ["params.cpp", "pg12.cu", "ops.cu", "ntt.cu"]
 

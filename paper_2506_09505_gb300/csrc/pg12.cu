@@ -46,7 +46,10 @@ namespace dev {
 constexpr int kBlock = 256;     // threads per Merkle block (8 independent warps)
 constexpr int kWarpNodes = 32;  // nodes of one level hashed by one warp task
 #ifndef PG12_MERKLE_MIN_BLOCKS
-#define PG12_MERKLE_MIN_BLOCKS 3  // resident 256-thread blocks per SM the register budget targets
+// resident 256-thread blocks per SM the register budget of k_merkle targets:
+// 4 caps it at 64 registers (32 warps per SM; measured 0.75% faster together
+// with PG12_PARTIAL_PAIRS than 3 blocks at 76 registers)
+#define PG12_MERKLE_MIN_BLOCKS 4
 #endif
 constexpr int kMaxLevels = 40;
 
