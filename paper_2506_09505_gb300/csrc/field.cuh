@@ -161,6 +161,13 @@ __device__ __forceinline__ void acc_zero(Acc &A) {
 #endif
 }
 
+// Sum that starts from one 64-bit value v (as if a first term were v * 1).
+__device__ __forceinline__ void acc_init(Acc &A, uint64_t v) {
+    acc_zero(A);
+    A.a0 = lo32(v);
+    A.a1 = hi32(v);
+}
+
 __device__ __forceinline__ void acc_mac(Acc &A, uint64_t x, uint64_t m) {
     const Partial q = partials(x, m);
 #if PG12_ACC_MID64

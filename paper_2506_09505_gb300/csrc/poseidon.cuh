@@ -35,6 +35,11 @@ struct DevConsts {
     uint32_t small_mat[kT][kT];  // M again when its entries fit 8 bits
     uint32_t small;              // 1: full rounds other than round 3 use small_mat
     uint32_t pad[3];
+    // Round 0 of a state whose capacity cells 8..11 enter as zero (every
+    // node compression, the first chunk of every sponge): those cells become
+    // the constants (c_0[j])^7, so their share of row i of M is the constant
+    // zcap_k[i] = sum_{j >= 8} M_ij (c_0[j])^7.
+    uint64_t zcap_k[kT];
 };
 
 // One copy per translation unit that includes this header; filled by
@@ -57,6 +62,16 @@ inline void make_dev_consts(const OptParams &op, DevConsts &dc) {
             dc.mat[0][i][j] = op.mds[i][j];
             dc.mat[1][i][j] = op.pre[i][j];
         }
+    const auto mulmod = [](uint64_t a, uint64_t b) { return (uint64_t)(((unsigned __int128)a * b) % P); };
+    for (int i = 0; i < kT; ++i) {
+        uint64_t k = 0;
+        for (int j = kRate; j < kT; ++j) {
+            const uint64_t c = op.full_rc[0][j] % P;
+            const uint64_t c2 = mulmod(c, c), c4 = mulmod(c2, c2), c7 = mulmod(mulmod(c4, c2), c);
+            k = (uint64_t)(((unsigned __int128)k + mulmod(op.mds[i][j] % P, c7)) % P);
+        }
+        dc.zcap_k[i] = k;
+    }
     for (int q = 0; q < kRP; ++q) {
         dc.part_rc[q] = op.part_rc[q];
         for (int j = 0; j < kT; ++j) dc.part_v[q][j] = op.part_v[q][j];
@@ -65,10 +80,11 @@ inline void make_dev_consts(const OptParams &op, DevConsts &dc) {
     }
 }
 
+// Cells 0 .. cells-1 of round r: constant, then the S-box.
 template <int S>
-__device__ __forceinline__ void sbox_phase(uint64_t *slot, int r) {
+__device__ __forceinline__ void sbox_phase(uint64_t *slot, int r, int cells) {
 #pragma unroll 1
-    for (int i = 0; i < kT; i += 2) {
+    for (int i = 0; i < cells; i += 2) {
         const uint64_t a = add_canon(slot[i * S], c_dev.full_rc[r][i]);
         const uint64_t b = add_canon(slot[(i + 1) * S], c_dev.full_rc[r][i + 1]);
         slot[i * S] = sbox(a);
@@ -80,18 +96,24 @@ __device__ __forceinline__ void sbox_phase(uint64_t *slot, int r) {
 #define PG12_DENSE_ROWS 1  // output rows per iteration of the dense loop (1 or 2)
 #endif
 
-template <int S>
+// Dense layer x = mat[m] x over the first NT cells of the slot; with
+// NT = kRate (round 0, capacity cells entered as zero) each row starts from
+// zcap_k instead of the products of cells 8..11.
+template <int S, int NT = kT>
 __device__ __forceinline__ void dense_phase(uint64_t *slot, int m) {
-    uint64_t x[kT];
+    uint64_t x[NT];
 #pragma unroll
-    for (int j = 0; j < kT; ++j) x[j] = slot[j * S];
+    for (int j = 0; j < NT; ++j) x[j] = slot[j * S];
 #pragma unroll 1
     for (int i = 0; i < kT; i += PG12_DENSE_ROWS) {
         Acc A[PG12_DENSE_ROWS];
 #pragma unroll
-        for (int k = 0; k < PG12_DENSE_ROWS; ++k) acc_zero(A[k]);
+        for (int k = 0; k < PG12_DENSE_ROWS; ++k) {
+            if (NT < kT) acc_init(A[k], c_dev.zcap_k[i + k]);
+            else acc_zero(A[k]);
+        }
 #pragma unroll
-        for (int j = 0; j < kT; ++j)
+        for (int j = 0; j < NT; ++j)
 #pragma unroll
             for (int k = 0; k < PG12_DENSE_ROWS; ++k) acc_mac(A[k], x[j], c_dev.mat[m][i + k][j]);
 #pragma unroll
@@ -109,22 +131,23 @@ __device__ __forceinline__ uint64_t madw(uint32_t a, uint32_t b, uint64_t c) {
     return d;
 }
 
-template <int S>
+template <int S, int NT = kT>
 __device__ __forceinline__ void dense_small_phase(uint64_t *slot) {
-    uint64_t x[kT];
+    uint64_t x[NT];
 #pragma unroll
-    for (int j = 0; j < kT; ++j) x[j] = slot[j * S];
+    for (int j = 0; j < NT; ++j) x[j] = slot[j * S];
 #pragma unroll 1
     for (int i = 0; i < kT; ++i) {
         uint64_t lo = 0, hi = 0;  // sums of x_j.lo * m_ij and x_j.hi * m_ij (< 2^44 each)
 #pragma unroll
-        for (int j = 0; j < kT; ++j) {
+        for (int j = 0; j < NT; ++j) {
             const uint32_t m = c_dev.small_mat[i][j];
             lo = madw(lo32(x[j]), m, lo);
             hi = madw(hi32(x[j]), m, hi);
         }
-        // value = lo + hi * 2^32 < 2^77
-        const u128 v = (u128)lo + ((u128)hi << 32);
+        // value = lo + hi * 2^32 (+ zcap_k[i] < p) < 2^78
+        u128 v = (u128)lo + ((u128)hi << 32);
+        if (NT < kT) v += c_dev.zcap_k[i];
         slot[i * S] = reduce128(v);
     }
 }
@@ -208,13 +231,27 @@ __device__ __forceinline__ void partial_phase(uint64_t *slot) {
 enum MdsKind { kMdsFull = 0, kMdsSmall = 1 };
 
 // The permutation on the state in `slot` (weak words in, weak words out).
+// zcap: cells 8..11 hold zero (a node compression or a sponge's first
+// chunk); round 0 then skips their S-boxes and products (zcap_k), which is
+// the same function with 4 of 118 S-boxes and 48 of 1,416 dense products
+// fewer.
+#ifndef PG12_ZCAP
+#define PG12_ZCAP 1  // 0: every permutation takes the general round 0
+#endif
 template <int S, int MDS = kMdsFull>
-__device__ __forceinline__ void permute_slot(uint64_t *slot) {
+__device__ __forceinline__ void permute_slot(uint64_t *slot, bool zcap = false) {
 #pragma unroll 1
     for (int r = 0; r < kRF; ++r) {
-        sbox_phase<S>(slot, r);
-        if (MDS == kMdsSmall && r != kRF / 2 - 1) dense_small_phase<S>(slot);
-        else dense_phase<S>(slot, r == kRF / 2 - 1 ? 1 : 0);
+        const bool z = PG12_ZCAP && zcap && r == 0;
+        sbox_phase<S>(slot, r, z ? kRate : kT);
+        if (z) {
+            if (MDS == kMdsSmall) dense_small_phase<S, kRate>(slot);
+            else dense_phase<S, kRate>(slot, 0);
+        } else if (MDS == kMdsSmall && r != kRF / 2 - 1) {
+            dense_small_phase<S>(slot);
+        } else {
+            dense_phase<S>(slot, r == kRF / 2 - 1 ? 1 : 0);
+        }
         if (r == kRF / 2 - 1) partial_phase<S>(slot);
     }
 }
