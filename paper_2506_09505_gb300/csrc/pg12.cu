@@ -115,7 +115,7 @@ __device__ __forceinline__ void sponge_slot(const uint64_t *row, uint64_t w, boo
         load_chunk(row, w, c, vec16, ch);
 #pragma unroll
         for (int i = 0; i < kRate; ++i) slot[i * S] = ch[i];
-        permute_slot<S, MDS>(slot, c == 0);
+        permute_slot<S, MDS>(slot, c == 0, c + 1 == chunks);
     }
 }
 
@@ -228,7 +228,7 @@ __device__ __forceinline__ void run_warp_task(const TreePlan &tp, uint32_t level
                 slot[(k + 1) * S] = b;
             }
         }
-        permute_slot<S, MDS>(slot, c == 0);
+        permute_slot<S, MDS>(slot, c == 0, c + 1 == nperm);
     }
     uint64_t *dst = tp.nodes + kDigest * (level_off(n, level) + i);
     st2(dst, canon(slot[0]), canon(slot[S]));
@@ -479,7 +479,7 @@ __global__ void __launch_bounds__(kVerifyBlock) k_merkle_verify(const uint64_t *
             slot[(kDigest + i) * kVerifyBlock] = right ? cur[i] : sib[i];
             slot[(2 * kDigest + i) * kVerifyBlock] = 0;
         }
-        permute_slot<kVerifyBlock, MDS>(slot, true);
+        permute_slot<kVerifyBlock, MDS>(slot, true, true);
         for (int i = 0; i < kDigest; ++i) cur[i] = canon(slot[i * kVerifyBlock]);
         pos >>= 1;
     }

@@ -100,12 +100,12 @@ __device__ __forceinline__ void sbox_phase(uint64_t *slot, int r, int cells) {
 // NT = kRate (round 0, capacity cells entered as zero) each row starts from
 // zcap_k instead of the products of cells 8..11.
 template <int S, int NT = kT>
-__device__ __forceinline__ void dense_phase(uint64_t *slot, int m) {
+__device__ __forceinline__ void dense_phase(uint64_t *slot, int m, int rows = kT) {
     uint64_t x[NT];
 #pragma unroll
     for (int j = 0; j < NT; ++j) x[j] = slot[j * S];
 #pragma unroll 1
-    for (int i = 0; i < kT; i += PG12_DENSE_ROWS) {
+    for (int i = 0; i < rows; i += PG12_DENSE_ROWS) {
         Acc A[PG12_DENSE_ROWS];
 #pragma unroll
         for (int k = 0; k < PG12_DENSE_ROWS; ++k) {
@@ -132,12 +132,12 @@ __device__ __forceinline__ uint64_t madw(uint32_t a, uint32_t b, uint64_t c) {
 }
 
 template <int S, int NT = kT>
-__device__ __forceinline__ void dense_small_phase(uint64_t *slot) {
+__device__ __forceinline__ void dense_small_phase(uint64_t *slot, int rows = kT) {
     uint64_t x[NT];
 #pragma unroll
     for (int j = 0; j < NT; ++j) x[j] = slot[j * S];
 #pragma unroll 1
-    for (int i = 0; i < kT; ++i) {
+    for (int i = 0; i < rows; ++i) {
         uint64_t lo = 0, hi = 0;  // sums of x_j.lo * m_ij and x_j.hi * m_ij (< 2^44 each)
 #pragma unroll
         for (int j = 0; j < NT; ++j) {
@@ -234,23 +234,29 @@ enum MdsKind { kMdsFull = 0, kMdsSmall = 1 };
 // zcap: cells 8..11 hold zero (a node compression or a sponge's first
 // chunk); round 0 then skips their S-boxes and products (zcap_k), which is
 // the same function with 4 of 118 S-boxes and 48 of 1,416 dense products
-// fewer.
+// fewer.  digest: only cells 0..3 of the result are read (a node, or a
+// sponge's last chunk); the last dense layer then computes rows 0..3 only
+// (96 products fewer) and leaves cells 4..11 holding S-box outputs.
 #ifndef PG12_ZCAP
 #define PG12_ZCAP 1  // 0: every permutation takes the general round 0
 #endif
+#ifndef PG12_DIGEST_ROWS
+#define PG12_DIGEST_ROWS 1  // 0: the last dense layer always computes all rows
+#endif
 template <int S, int MDS = kMdsFull>
-__device__ __forceinline__ void permute_slot(uint64_t *slot, bool zcap = false) {
+__device__ __forceinline__ void permute_slot(uint64_t *slot, bool zcap = false, bool digest = false) {
 #pragma unroll 1
     for (int r = 0; r < kRF; ++r) {
         const bool z = PG12_ZCAP && zcap && r == 0;
+        const int rows = PG12_DIGEST_ROWS && digest && r == kRF - 1 ? kDigest : kT;
         sbox_phase<S>(slot, r, z ? kRate : kT);
         if (z) {
             if (MDS == kMdsSmall) dense_small_phase<S, kRate>(slot);
             else dense_phase<S, kRate>(slot, 0);
         } else if (MDS == kMdsSmall && r != kRF / 2 - 1) {
-            dense_small_phase<S>(slot);
+            dense_small_phase<S>(slot, rows);
         } else {
-            dense_phase<S>(slot, r == kRF / 2 - 1 ? 1 : 0);
+            dense_phase<S>(slot, r == kRF / 2 - 1 ? 1 : 0, rows);
         }
         if (r == kRF / 2 - 1) partial_phase<S>(slot);
     }
