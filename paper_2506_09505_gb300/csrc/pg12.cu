@@ -198,8 +198,11 @@ __global__ void __launch_bounds__(kSmallBlock) k_merkle_level(const uint64_t *__
 // -- a row through the sponge at level 0, else the pair of children at
 // level l-1 -- in the lane's shared-memory state slot (stride S = threads
 // per block).  Both cases feed one permutation call site, so the kernel holds
-// a single copy of the permutation code.
-template <int S, int MDS>
+// a single copy of the permutation code.  ZC: the first permutation of a task
+// takes the zero-capacity round 0 (a second copy of round 0's dense layer in
+// the kernel; measured a gain where every warp hashes single-chunk leaves, a
+// loss of 7% in the batched launch, where warps sit in different phases).
+template <int S, int MDS, bool ZC = false>
 __device__ __forceinline__ void run_warp_task(const TreePlan &tp, uint32_t level, uint64_t u, int lane,
                                               uint64_t *slot) {
     const uint64_t n = tp.n_leaves;
@@ -228,7 +231,7 @@ __device__ __forceinline__ void run_warp_task(const TreePlan &tp, uint32_t level
                 slot[(k + 1) * S] = b;
             }
         }
-        permute_slot<S, MDS>(slot, c == 0, c + 1 == nperm);
+        permute_slot<S, MDS>(slot, ZC && c == 0, c + 1 == nperm);
     }
     uint64_t *dst = tp.nodes + kDigest * (level_off(n, level) + i);
     st2(dst, canon(slot[0]), canon(slot[S]));
@@ -252,7 +255,7 @@ __device__ __forceinline__ void signal_root(const TreePlan &tp, int lane) {
 // the parent and keeps climbing; the first arriver goes back for a new leaf
 // task.  Levels with at most 32 nodes have a single task and are climbed
 // without counters.  No block-wide barrier and no waiting anywhere.
-template <int S, int MDS>
+template <int S, int MDS, bool ZC = false>
 __global__ void __launch_bounds__(S, PG12_MERKLE_MIN_BLOCKS * 256 / S) k_merkle(const TreePlan *__restrict__ plans, uint32_t n_trees,
                                              uint32_t total_tasks, uint32_t *__restrict__ counters,
                                              uint32_t *__restrict__ next_task) {
@@ -276,7 +279,7 @@ __global__ void __launch_bounds__(S, PG12_MERKLE_MIN_BLOCKS * 256 / S) k_merkle(
         const uint64_t n = tp.n_leaves;
         const uint32_t log_n = tp.log_n;
         uint64_t u = task - tp.leaf_task_begin;
-        run_warp_task<S, MDS>(tp, 0, u, lane, slot);
+        run_warp_task<S, MDS, ZC>(tp, 0, u, lane, slot);
         if (log_n == 0) signal_root(tp, lane);
         const uint32_t top = log_n < tp.climb_limit ? log_n : tp.climb_limit;
         for (uint32_t level = 1; level <= top; ++level) {
@@ -294,7 +297,7 @@ __global__ void __launch_bounds__(S, PG12_MERKLE_MIN_BLOCKS * 256 / S) k_merkle(
                 __syncwarp();
             }
             u >>= 1;
-            run_warp_task<S, MDS>(tp, level, u, lane, slot);
+            run_warp_task<S, MDS, ZC>(tp, level, u, lane, slot);
             if (level == log_n) signal_root(tp, lane);
         }
     }
@@ -771,7 +774,7 @@ pg_status launch_leaves(const uint64_t *rows, uint64_t n, uint64_t width, uint64
 
 // Launch the persistent Merkle kernel for `tasks` leaf tasks.
 pg_status launch_merkle(const pg_schedule *sched, const dev::TreePlan *d_plans, uint32_t n_trees, uint32_t tasks,
-                        uint32_t *d_counters, cudaStream_t st, uint64_t perms) {
+                        uint32_t *d_counters, cudaStream_t st, uint64_t perms, bool zcap = false) {
     const uint32_t block = (sched && sched->block == 128) ? 128u : 256u;
     const int occ = block == 128 ? g.merkle128_blocks_per_sm : g.merkle_blocks_per_sm;
     int bps = occ;
@@ -787,8 +790,14 @@ pg_status launch_merkle(const pg_schedule *sched, const dev::TreePlan *d_plans, 
         if (small) dev::k_merkle<128, dev::kMdsSmall><<<grid, 128, 0, st>>>(d_plans, n_trees, tasks, d_counters + 1, d_counters);
         else dev::k_merkle<128, dev::kMdsFull><<<grid, 128, 0, st>>>(d_plans, n_trees, tasks, d_counters + 1, d_counters);
     } else {
-        if (small) dev::k_merkle<256, dev::kMdsSmall><<<grid, 256, 0, st>>>(d_plans, n_trees, tasks, d_counters + 1, d_counters);
-        else dev::k_merkle<256, dev::kMdsFull><<<grid, 256, 0, st>>>(d_plans, n_trees, tasks, d_counters + 1, d_counters);
+        if (zcap && small)
+            dev::k_merkle<256, dev::kMdsSmall, true><<<grid, 256, 0, st>>>(d_plans, n_trees, tasks, d_counters + 1, d_counters);
+        else if (zcap)
+            dev::k_merkle<256, dev::kMdsFull, true><<<grid, 256, 0, st>>>(d_plans, n_trees, tasks, d_counters + 1, d_counters);
+        else if (small)
+            dev::k_merkle<256, dev::kMdsSmall><<<grid, 256, 0, st>>>(d_plans, n_trees, tasks, d_counters + 1, d_counters);
+        else
+            dev::k_merkle<256, dev::kMdsFull><<<grid, 256, 0, st>>>(d_plans, n_trees, tasks, d_counters + 1, d_counters);
     }
     PG_CUDA(cudaGetLastError());
     return PG_OK;
@@ -1195,9 +1204,13 @@ pg_status pg_init(int device, const char *params_path) {
     }
     PG_CUDA(cudaDeviceGetAttribute(&g.sms, cudaDevAttrMultiProcessorCount, device));
     {
-        int a = 0, b = 0, c = 0, d = 0, e = 0, f = 0;
+        int a = 0, b = 0, c = 0, d = 0, e = 0, f = 0, za = 0, zb = 0;
         PG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, dev::k_merkle<256, dev::kMdsFull>, 256, 0));
         PG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, dev::k_merkle<256, dev::kMdsSmall>, 256, 0));
+        PG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&za, dev::k_merkle<256, dev::kMdsFull, true>, 256, 0));
+        PG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&zb, dev::k_merkle<256, dev::kMdsSmall, true>, 256, 0));
+        a = a < za ? a : za;
+        b = b < zb ? b : zb;
         PG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, dev::k_merkle<128, dev::kMdsFull>, 128, 0));
         PG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d, dev::k_merkle<128, dev::kMdsSmall>, 128, 0));
         PG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&e, dev::k_permute<dev::kMdsFull>, dev::kSmallBlock, 0));
@@ -1318,7 +1331,7 @@ pg_status pg_merkle_build(const uint64_t *rows, size_t n_leaves, size_t width, u
         PG_CUDA(cudaMemsetAsync(d_counters, 0, tp.climb_limit ? counter_bytes : sizeof(uint32_t), st));
         // leaf sponges plus the nodes of levels 1 .. first_top-1
         const uint64_t perms = tree_perms(n_leaves, width) - ((n_leaves >> (first_top - 1)) - 1);
-        s = launch_merkle(nullptr, d_plan, 1u, tasks, d_counters, st, perms);
+        s = launch_merkle(nullptr, d_plan, 1u, tasks, d_counters, st, perms, true);
         if (s != PG_OK) return s;
     }
     s = launch_levels(nodes, n_leaves, first_top, st);
