@@ -56,10 +56,10 @@ L2_BYTES = 129 * 10**6  # GB300 L2
 # kernel of a tree build, averaged over its launches in one ncu capture of the
 # current kernels on that workload (params, log2 leaves, width); other
 # workloads report null.
-KERNEL_TRAFFIC = {("pg12_v1", 22, 8, "k_merkle"): 372_573_988,
-                  ("pg12_v1", 22, 8, "k_merkle_level"): 37_481_530,
-                  ("pg12_v1", 22, 8, "k_merkle_top"): 173_714,
-                  ("pg12_v1", 22, 8, "k_merkle_top_tail"): 40_192}
+KERNEL_TRAFFIC = {("pg12_v1", 22, 8, "k_merkle"): 373_116_562,
+                  ("pg12_v1", 22, 8, "k_merkle_level"): 37_407_000,
+                  ("pg12_v1", 22, 8, "k_merkle_top"): 173_674,
+                  ("pg12_v1", 22, 8, "k_merkle_top_tail"): 40_554}
 
 
 def algorithmic_bytes(kernel, perms_per_launch, width):
