@@ -55,6 +55,12 @@ constexpr int kMaxT = 11;        // stages per pass
 #ifndef PG12_NTT_TILE_BITS8
 #define PG12_NTT_TILE_BITS8 10   // log2 tile rows with eight columns (64 KiB of words)
 #endif
+#ifndef PG12_NTT_RADIX8
+#define PG12_NTT_RADIX8 1        // 1: three stages per shared-memory round trip where they fit
+#endif
+#ifndef PG12_NTT_NO_R2
+#define PG12_NTT_NO_R2 1         // 1: split 4 remaining stages 2 + 2 instead of 3 + 1
+#endif
 constexpr int kMaxU = PG12_NTT_MAXU;  // a tile spans up to 2^kMaxU consecutive values of the low bits
 constexpr int kMaxLogC = 3;      // and at most 8 columns
 constexpr int kThreads = 256;
@@ -201,6 +207,64 @@ __global__ void __launch_bounds__(kThreads) k_ntt_pass(const Pass ps) {
     __syncthreads();
 
     uint32_t done = 0;
+#if PG12_NTT_RADIX8
+    // Three stages between barriers (radix 8: eight rows per thread, twelve
+    // butterflies): stage b needs one twiddle per group, stage b + 1 two and
+    // stage b + 2 four, indexed by the row bits below each stage's bit.
+    // (four stages left go as two radix-4 steps rather than radix 8 and a
+    // lone radix-2 stage)
+    const uint32_t groups8 = (rows >> 3) << (u + LOG_C);
+    while (done + 3 <= t && (!PG12_NTT_NO_R2 || t - done != 4)) {
+        const uint32_t b = DIT ? done : t - 3 - done;  // lowest bit of the three
+        const uint32_t m0 = (1u << b) - 1, m1 = (2u << b) - 1, m2 = (4u << b) - 1;
+        const uint32_t s0 = 1u << (b + u + LOG_C), s1 = 2u << (b + u + LOG_C), s2 = 4u << (b + u + LOG_C);
+        for (uint32_t p = threadIdx.x; p < groups8; p += kThreads) {
+            const uint32_t lc = p & ((C << u) - 1), g = p >> (u + LOG_C);
+            const uint32_t v0 = ((g >> b) << (b + 3)) | (g & m0);
+            uint64_t *x = tile + ((v0 << (u + LOG_C)) + lc);
+            const uint64_t *w = tw + ((lc >> LOG_C) << t);
+            const uint32_t k = v0 & m0;
+            uint64_t a[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) a[i] = x[(i & 1) * s0 + ((i >> 1) & 1) * s1 + (i >> 2) * s2];
+            const uint64_t w0 = w[m0 + k];                                  // stage b
+            const uint64_t w10 = w[m1 + k], w11 = w[m1 + k + (1u << b)];    // stage b + 1
+            const uint64_t w20 = w[m2 + k], w21 = w[m2 + k + (1u << b)];    // stage b + 2
+            const uint64_t w22 = w[m2 + k + (2u << b)], w23 = w[m2 + k + (3u << b)];
+            if (DIT) {
+                bfly<1>(a[0], a[1], w0);
+                bfly<1>(a[2], a[3], w0);
+                bfly<1>(a[4], a[5], w0);
+                bfly<1>(a[6], a[7], w0);
+                bfly<1>(a[0], a[2], w10);
+                bfly<1>(a[1], a[3], w11);
+                bfly<1>(a[4], a[6], w10);
+                bfly<1>(a[5], a[7], w11);
+                bfly<1>(a[0], a[4], w20);
+                bfly<1>(a[1], a[5], w21);
+                bfly<1>(a[2], a[6], w22);
+                bfly<1>(a[3], a[7], w23);
+            } else {
+                bfly<0>(a[0], a[4], w20);
+                bfly<0>(a[1], a[5], w21);
+                bfly<0>(a[2], a[6], w22);
+                bfly<0>(a[3], a[7], w23);
+                bfly<0>(a[0], a[2], w10);
+                bfly<0>(a[1], a[3], w11);
+                bfly<0>(a[4], a[6], w10);
+                bfly<0>(a[5], a[7], w11);
+                bfly<0>(a[0], a[1], w0);
+                bfly<0>(a[2], a[3], w0);
+                bfly<0>(a[4], a[5], w0);
+                bfly<0>(a[6], a[7], w0);
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i) x[(i & 1) * s0 + ((i >> 1) & 1) * s1 + (i >> 2) * s2] = a[i];
+        }
+        __syncthreads();
+        done += 3;
+    }
+#endif
     const uint32_t groups = (rows >> 2) << (u + LOG_C);
     while (done + 2 <= t) {
         const uint32_t b = DIT ? done : t - 2 - done;  // lower bit of the pair
