@@ -17,7 +17,10 @@
 // inputs in registers while it loops over output rows, fetching each row's
 // constants with uniform loads and storing each output straight back to
 // the slot.  Dense rows are accumulated lazily (twelve 128-bit products,
-// one reduction per output cell).
+// one reduction per output cell).  Where the caller knows more about the
+// state (its capacity cells enter as zero, or only the digest cells of the
+// result are read) the first and last rounds skip the work that knowledge
+// makes constant or unused (permute_slot).
 #pragma once
 #include "field.cuh"
 #include "pg12_internal.h"
