@@ -62,6 +62,45 @@ def test_optimised_form_equals_plain_permutation(lib):
         assert _opt_permute(st[k], op) == [int(v) for v in want[k]]
 
 
+def _opt_compress(x8, op):
+    """The library's shortcut for a state [x8, 0, 0, 0, 0] whose digest is all
+    that is read: round 0 takes the capacity cells' share of each dense row as
+    one constant (their S-box inputs are the round constants alone), and the
+    last dense layer computes rows 0..3 only."""
+    fr, M, pre = op["full_rc"], op["mds"], op["pre"]
+    k = [sum(int(M[i, j]) * pow(int(fr[0, j]), 7, P) for j in range(8, 12)) % P for i in range(12)]
+    y = [pow((int(x8[j]) + int(fr[0, j])) % P, 7, P) for j in range(8)]
+    x = [(k[i] + sum(int(M[i, j]) * y[j] for j in range(8))) % P for i in range(12)]
+
+    def full(x, r, mat, rows=12):
+        y = [pow((x[i] + int(fr[r, i])) % P, 7, P) for i in range(12)]
+        return [sum(int(mat[i, j]) * y[j] for j in range(12)) % P for i in range(rows)]
+    for r in (1, 2):
+        x = full(x, r, M)
+    x = full(x, 3, pre)
+    for q in range(22):
+        x0 = pow((x[0] + int(op["part_rc"][q])) % P, 7, P)
+        v, w = op["part_v"][q], op["part_w"][q]
+        new0 = (int(v[0]) * x0 + sum(int(v[j]) * x[j] for j in range(1, 12))) % P
+        x = [new0] + [(x[i] + int(w[i - 1]) * x0) % P for i in range(1, 12)]
+    for r in (4, 5, 6):
+        x = full(x, r, M)
+    return full(x, 7, M, rows=4)
+
+
+def test_zero_capacity_digest_shortcut_equals_plain_permutation(lib):
+    # node compressions and single-chunk leaves: [8 words, 0^4] -> first 4 words
+    op = pg.params_export_optimized()
+    st = pg_synth.matrix(0xAC, 24, 12, bound=None)
+    st[:, 8:] = 0
+    want = oracle.permute(st)
+    for k in range(st.shape[0]):
+        assert _opt_compress(st[k, :8], op) == [int(v) for v in want[k, :4]]
+    left, right = pg_synth.matrix(0xAD, 1, 4)[0], pg_synth.matrix(0xAE, 1, 4)[0]
+    node = oracle.hash_pair(left, right)
+    assert _opt_compress(np.concatenate([left, right]), op) == [int(v) for v in node]
+
+
 def test_optimised_constants_canonical(lib):
     op = pg.params_export_optimized()
     for name, a in op.items():
