@@ -49,7 +49,10 @@ ZCAP_SAVED = 4 * (2 * 6 + 2 * 8) + 48 * 8
 ZCAP_SAVED_SMALL = 4 * (2 * 6 + 2 * 8) + 48 * 4
 DIGEST_SAVED = 96 * 8
 DIGEST_SAVED_SMALL = 96 * 4
-ZCAP_KERNELS = ("k_merkle", "k_merkle_level", "k_hash_rows")
+ZCAP_KERNELS = ("k_merkle", "k_merkle_level", "k_hash_rows", "k_tc_sponge:leaves", "k_tc_sponge:level",
+                "k_tc_sponge:rows")
+LEVEL_KERNELS = ("k_merkle_level", "k_tc_sponge:level")
+LEAF_KERNELS = ("k_merkle", "k_merkle_top_leaf", "k_tc_sponge:leaves")
 IMAD_RESULTS_PER_CLK_SM = 64  # 32-bit multiply results per clock per SM
 L2_BYTES = 129 * 10**6  # GB300 L2
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of each
@@ -65,7 +68,7 @@ KERNEL_TRAFFIC = {("pg12_v1", 22, 8, "k_merkle"): 373_116_562,
 def algorithmic_bytes(kernel, perms_per_launch, width):
     """Bytes a launch must move: rows read and digests written (leaves), or two
     child digests read and one written per node (levels)."""
-    if kernel in ("k_merkle", "k_merkle_top_leaf"):
+    if kernel in LEAF_KERNELS:
         leaves = perms_per_launch // max(1, (width + 7) // 8)
         return leaves * (8 * width + 32)
     return perms_per_launch * 96
@@ -395,7 +398,7 @@ def run_ours(args):
         # in a digest; leaf launches: the first and the last of each leaf's chunks
         if name not in ZCAP_KERNELS:
             return mul_per_perm
-        share = 1.0 if name == "k_merkle_level" else 1.0 / chunks
+        share = 1.0 if name in LEVEL_KERNELS else 1.0 / chunks
         return mul_per_perm - share * saved
 
     def kernel_roofline(name):

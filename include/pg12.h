@@ -148,6 +148,52 @@ pg_status pg_params_select(const char *name);
 /* Name of the active parameter set. */
 const char *pg_params_name(void);
 
+/*
+ * Permutation engines (the computed function is the same; results are
+ * bit-identical):
+ *   PG_ENGINE_INT     every step on the integer pipes (Alg. 1 with the
+ *                     special-prime reduction of Alg. 2, one thread per state);
+ *   PG_ENGINE_TENSOR  the same, except that the 12x12 MDS products of the
+ *                     eight full rounds (Alg. 1, MDS) of 128 states at a time
+ *                     are one exact tensor-core contraction of byte limbs
+ *                     (fp16 operands, fp32 sums of integers below 2^24) --
+ *                     used by pg_permute_batch, pg_hash_rows, the leaves of
+ *                     pg_merkle_build / pg_merkle_build_host and their tree
+ *                     levels of at least 2^15 nodes.  The default.
+ * pg_set_engine applies to launches made after it returns; PG_ERR_INVALID_ARG
+ * for any other value.  Host-only.
+ */
+/*
+ * pg_tc_tables_export -- host copy of the tensor-core digit tables of the
+ * active parameter set, for inspection and CPU tests: with out == NULL
+ * returns the table size in bytes; else writes it to `out` (host, `bytes`
+ * long) and returns it, or returns 0 if `bytes` is too small.  Layout (all
+ * little-endian fp16 bit patterns, K-major 8x8 core matrices of 128 bytes):
+ *   b[2][96 rows n = 8i+b][14 chunks]  balanced base-256 digit b of
+ *       2^(8a) m_ij mod p at column 8j+a (chunks 0..11; matrix 0 = M of the
+ *       full rounds, 1 = round 3's transition matrix), chunk 12 column 0 =
+ *       4 u_b (the bias), the rest zero; core matrix (n/8, c) at byte
+ *       (n/8 * 14 + c) * 128, row n%8 at 16 (n%8);
+ *   a_bias[2 core matrices]  2^-13 at column 0 of every row;
+ *   a_zcap[4 core matrices]  bytes of (c_0[j])^7, j = 8..11, every row.
+ * Host-only; works without a GPU.
+ */
+size_t pg_tc_tables_export(void *out, size_t bytes);
+
+#define PG_ENGINE_INT 0
+#define PG_ENGINE_TENSOR 1
+pg_status pg_set_engine(int engine);
+int pg_get_engine(void);
+
+/*
+ * pg_device_faults -- *faults = 1 if a tensor-core kernel launched since the
+ * last call gave up waiting for its tensor cores (each such wait is bounded,
+ * about two seconds; the kernel then stops and frees its tensor memory, and
+ * its outputs are not valid), else 0; the flag is cleared.  Synchronous (it
+ * reads a device word).  PG_ERR_NOT_INIT before pg_init.
+ */
+pg_status pg_device_faults(uint32_t *faults);
+
 /* Release the workspace.  Safe to call when not initialised. */
 pg_status pg_shutdown(void);
 

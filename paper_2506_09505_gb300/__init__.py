@@ -80,6 +80,10 @@ SIGNATURES = {
     "pg_init": (ctypes.c_int, [ctypes.c_int, ctypes.c_char_p]),
     "pg_params_select": (ctypes.c_int, [ctypes.c_char_p]),
     "pg_params_name": (ctypes.c_char_p, []),
+    "pg_set_engine": (ctypes.c_int, [ctypes.c_int]),
+    "pg_tc_tables_export": (ctypes.c_size_t, [ctypes.c_void_p, ctypes.c_size_t]),
+    "pg_get_engine": (ctypes.c_int, []),
+    "pg_device_faults": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint32)]),
     "pg_shutdown": (ctypes.c_int, []),
     "pg_params_export": (ctypes.c_int, [_u64p, _u64p]),
     "pg_params_export_optimized": (ctypes.c_int, [_u64p] * 6),
@@ -206,6 +210,34 @@ def params_name() -> str:
 
 def shutdown() -> None:
     _check(load().pg_shutdown())
+
+
+ENGINE_INT, ENGINE_TENSOR = 0, 1
+
+
+def set_engine(engine: int) -> None:
+    """Permutation engine of later launches: ENGINE_TENSOR (default) or ENGINE_INT."""
+    _check(load().pg_set_engine(int(engine)))
+
+
+def get_engine() -> int:
+    return int(load().pg_get_engine())
+
+
+def tc_tables_export() -> bytes:
+    """The tensor-core digit tables of the active parameter set (see include/pg12.h)."""
+    n = int(load().pg_tc_tables_export(None, 0))
+    buf = ctypes.create_string_buffer(n)
+    if int(load().pg_tc_tables_export(buf, n)) != n:
+        raise PGError(6, "tensor-core tables unavailable: " + last_error())
+    return buf.raw
+
+
+def device_faults() -> int:
+    """1 if a tensor-core wait ran out since the last call (then cleared), else 0."""
+    v = ctypes.c_uint32(0)
+    _check(load().pg_device_faults(ctypes.byref(v)))
+    return int(v.value)
 
 
 def _dev_ptr(t, name: str) -> int:

@@ -287,6 +287,91 @@ bool derive_optimized(const PlainParams &pp, OptParams &op) {
     return true;
 }
 
+// ------------------------------------------------------------ tensor-core digit tables
+namespace {
+
+// fp16 bits of a nonzero integer below 2^16 with at most 11 significant bits
+// (exactly representable).
+uint16_t half_of_int(int v) {
+    if (v == 0) return 0;
+    const uint16_t sign = v < 0 ? 0x8000u : 0u;
+    uint32_t m = (uint32_t)(v < 0 ? -v : v);
+    int e = 0;
+    while ((m >> e) > 1) ++e;  // 2^e <= m < 2^(e+1)
+    const uint32_t frac = (e <= 10 ? m << (10 - e) : m >> (e - 10)) & 0x3FFu;  // 10 fraction bits
+    return (uint16_t)(sign | ((uint32_t)(e + 15) << 10) | frac);
+}
+
+// Eight balanced base-256 digits of a residue: the representative v in
+// [-128 (2^64-1)/255, 127 (2^64-1)/255] (an interval of 2^64 - 1 > p
+// integers) written as sum_b d_b 256^b with d_b in [-128, 127].
+void balanced_digits(uint64_t r, int d[8]) {
+    const unsigned __int128 hi = (unsigned __int128)127 * 0x0101010101010101ull;
+    __int128 v = (unsigned __int128)r <= hi ? (__int128)r : (__int128)r - (__int128)kP;
+    for (int b = 0; b < 8; ++b) {
+        __int128 q = v >= 0 ? v / 256 : -((-v + 255) / 256);  // floor(v / 256)
+        int rem = (int)(v - q * 256);                          // in [0, 256)
+        if (rem >= 128) {
+            rem -= 256;
+            ++q;
+        }
+        d[b] = rem;
+        v = q;
+    }
+}
+
+}  // namespace
+
+void build_tc_tables(const OptParams &op, TcTables &tt) {
+    std::memset(&tt, 0, sizeof tt);
+    // Bias digits u_b: column (i, b) reads back bits = 0x3E800000 + magic_b + Z
+    // with magic_b = 8192 u_b (A bias 2^-13 times B bias 4 u_b, values scaled by
+    // 2^-24), and sum_b 2^(8b) (0x3E800000 + 8192 u_b) = 0 (mod p) is solved for
+    // u_b in [1407, 1665], the range that keeps magic_b + Z in [2^23, 2^24) for
+    // |Z| <= 3133440.  The sums sum_b u_b 2^(8b) cover every integer from
+    // 1407 G to 1665 G (G = sum_b 2^(8b); 259 digit values for radix 256), an
+    // interval longer than p, so a solution exists.
+    typedef unsigned __int128 u128;
+    const uint64_t G = 0x0101010101010101ull;
+    const uint64_t Gp = G % kP;
+    const uint64_t c0 = fp_mul(0x3E800000ull, Gp);              // sum_b 2^(8b) 0x3E800000 mod p
+    const uint64_t t = fp_mul(fp_sub(0, c0), fp_inv(8192));     // wanted sum_b u_b 2^(8b) mod p
+    const u128 umin = (u128)1407 * G;
+    const uint64_t umin_p = (uint64_t)(umin % kP);
+    u128 rest = fp_sub(t, umin_p);                               // U - umin, in [0, p)
+    int u[8];
+    for (int b = 7; b >= 0; --b) {
+        const u128 w = (u128)1 << (8 * b);
+        u128 e = rest / w;
+        if (e > 258) e = 258;
+        rest -= e * w;
+        u[b] = 1407 + (int)e;
+    }
+    for (int m = 0; m < 2; ++m) {
+        uint16_t *B = tt.b[m];
+        for (int i = 0; i < kT; ++i)
+            for (int j = 0; j < kT; ++j) {
+                const uint64_t mij = (m == 0 ? op.mds[i][j] : op.pre[i][j]) % kP;
+                for (int a = 0; a < 8; ++a) {
+                    int d[8];
+                    balanced_digits(fp_mul(mij, fp_pow(2, 8 * (uint64_t)a)), d);
+                    for (int b = 0; b < 8; ++b) {
+                        const int n = 8 * i + b, c = j;  // k = 8 j + a: chunk j, column a
+                        B[(n / 8 * kTcKC + c) * 64 + (n % 8) * 8 + a] = half_of_int(d[b]);
+                    }
+                }
+            }
+        for (int n = 0; n < kTcN; ++n) B[(n / 8 * kTcKC + 12) * 64 + (n % 8) * 8] = half_of_int(4 * u[n % 8]);
+    }
+    for (int r = 0; r < 8; ++r) tt.a_bias[r * 8] = 0x0800;  // 2^-13
+    for (int j = kRate; j < kT; ++j) {
+        const uint64_t c = op.full_rc[0][j] % kP;
+        const uint64_t c7 = fp_pow(c, 7);
+        for (int r = 0; r < 8; ++r)
+            for (int a = 0; a < 8; ++a) tt.a_zcap[(j - kRate) * 64 + r * 8 + a] = (uint16_t)((c7 >> (8 * a)) & 0xFF);
+    }
+}
+
 // ------------------------------------------------------------ SHA-256
 // FIPS 180-4 SHA-256 of a byte string, used to fingerprint a parameter set.
 // Its constants are computed from their definition rather than tabulated:

@@ -22,6 +22,7 @@
 #include "pg12.h"
 #include "pg12_internal.h"
 #include "poseidon.cuh"
+#include "tc_perm.cuh"
 
 #include <cuda_runtime.h>
 
@@ -192,6 +193,91 @@ __global__ void __launch_bounds__(kSmallBlock) k_merkle_level(const uint64_t *__
         st2(here + kDigest * k, canon(slot[0]), canon(slot[kSmallBlock]));
         st2(here + kDigest * k + 2, canon(slot[2 * kSmallBlock]), canon(slot[3 * kSmallBlock]));
     }
+}
+
+// ------------------------------------------------- tensor-core kernels
+// Persistent kernels of kTcGroups groups of 128 threads (one CTA per SM:
+// its tables, operands and slots take ~187 KiB of shared memory and its
+// groups all 512 columns of tensor memory).  Group q of CTA c takes units
+// c * kTcGroups + q, then every gridDim.x * kTcGroups-th after: a static
+// schedule with no shared counter, so launches on different streams are
+// independent.  A unit is 128 consecutive states or rows; rows past the end
+// are computed on zeros and not stored.
+constexpr int kTcGroups = 4;
+constexpr int kTcThreads = kTcGroup * kTcGroups;
+using TcL = TcLayout<kTcGroups>;
+
+__global__ void __launch_bounds__(kTcThreads, 1) k_tc_permute(uint64_t *__restrict__ st, uint64_t n, int vec16) {
+    extern __shared__ __align__(1024) uint8_t tc_sm[];
+    TcGroup G = tc_setup<kTcGroups>(tc_sm);
+    uint64_t *slot = G.slot + G.t;
+    const uint64_t units = (n + kTcGroup - 1) / kTcGroup;
+    const uint64_t step = (uint64_t)gridDim.x * kTcGroups;
+    for (uint64_t u = (uint64_t)blockIdx.x * kTcGroups + threadIdx.x / kTcGroup; u < units; u += step) {
+        const uint64_t k = u * kTcGroup + G.t;
+        const bool valid = k < n;
+        uint64_t *p = st + kT * k;
+        if (valid && vec16) {
+#pragma unroll
+            for (int i = 0; i < kT; i += 2) {
+                uint64_t a, b;
+                ld2_nc(p + i, a, b);
+                slot[i * kTcGroup] = a;
+                slot[(i + 1) * kTcGroup] = b;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < kT; ++i) slot[i * kTcGroup] = valid ? p[i] : 0ull;
+        }
+        if (!tc_permute(G, false, false)) break;
+        if (valid) {
+            if (vec16) {
+#pragma unroll
+                for (int i = 0; i < kT; i += 2) st2(p + i, canon(slot[i * kTcGroup]), canon(slot[(i + 1) * kTcGroup]));
+            } else {
+#pragma unroll
+                for (int i = 0; i < kT; ++i) p[i] = canon(slot[i * kTcGroup]);
+            }
+        }
+    }
+    tc_teardown<kTcGroups>(tc_sm, G);
+}
+
+// Sponge digests of n rows of width w (Sec. 2.4): the leaves of a tree, or a
+// tree level (the level below read as rows of its children's 8 words), or
+// pg_hash_rows.  Launched as a dependent launch it may set up while the
+// kernel before it finishes, and reads `rows` only after pdl_wait().
+__global__ void __launch_bounds__(kTcThreads, 1) k_tc_sponge(const uint64_t *__restrict__ rows, uint64_t n, uint64_t w,
+                                                             int vec16, uint64_t *__restrict__ out) {
+    extern __shared__ __align__(1024) uint8_t tc_sm[];
+    pdl_trigger();
+    TcGroup G = tc_setup<kTcGroups>(tc_sm);
+    pdl_wait();
+    uint64_t *slot = G.slot + G.t;
+    const uint64_t units = (n + kTcGroup - 1) / kTcGroup;
+    const uint64_t step = (uint64_t)gridDim.x * kTcGroups;
+    const uint64_t chunks = (w + kRate - 1) / kRate;
+    for (uint64_t u = (uint64_t)blockIdx.x * kTcGroups + threadIdx.x / kTcGroup; u < units; u += step) {
+        const uint64_t r = u * kTcGroup + G.t;
+        const bool valid = r < n;
+        const uint64_t *row = rows + (valid ? r : 0) * w;
+#pragma unroll
+        for (int i = kRate; i < kT; ++i) slot[i * kTcGroup] = 0;
+        bool ok = true;
+        for (uint64_t c = 0; c < chunks && ok; ++c) {
+            uint64_t ch[kRate];
+            load_chunk(row, w, c, vec16 != 0, ch);
+#pragma unroll
+            for (int i = 0; i < kRate; ++i) slot[i * kTcGroup] = valid ? ch[i] : 0ull;
+            ok = tc_permute(G, c == 0, c + 1 == chunks);
+        }
+        if (!ok) break;
+        if (valid) {
+            st2(out + kDigest * r, canon(slot[0]), canon(slot[kTcGroup]));
+            st2(out + kDigest * r + 2, canon(slot[2 * kTcGroup]), canon(slot[3 * kTcGroup]));
+        }
+    }
+    tc_teardown<kTcGroups>(tc_sm, G);
 }
 
 // One warp task: lane i of task u at level l hashes node 32u+i of that level
@@ -511,6 +597,10 @@ struct Context {
     int permute_blocks_per_sm = 0;
     uint8_t *ws = nullptr;  // device workspace
     size_t ws_bytes = 0;
+    // 1: permutations of batches, rows, leaves and large levels run their full
+    // rounds' dense layers on the tensor cores; 0: integer pipes only
+    int engine = 1;
+    uint64_t tc_min_nodes = 1ull << 15;  // smallest tree level built by the tensor-core kernel
     cudaStream_t copy_st = nullptr;  // host-row copies of pg_merkle_build_host
     cudaEvent_t host_ev[17] = {};    // one per chunk, plus "previous work done"
 };
@@ -573,7 +663,9 @@ const char *const kKernelNames[kIdCount] = {"k_merkle",      "k_merkle_top",    
                                             "k_permute",     "k_hash_rows",     "k_merkle_open",
                                             "k_merkle_verify", "k_merkle_single", "batch_graph",
                                             "k_ntt_pass",    "k_ntt_bitrev",    "k_merkle_level",
-                                            "k_merkle_top_tail"};
+                                            "k_merkle_top_tail",
+                                            "k_tc_permute",  "k_tc_sponge:leaves", "k_tc_sponge:level",
+                                            "k_tc_sponge:rows"};
 constexpr size_t kProfMaxRecords = 1u << 16;
 
 struct ProfRecord {
@@ -621,6 +713,20 @@ pg_status ensure_params() {
         return fail(PG_ERR_PARAMS, "parameter set %s: sparse rewrite failed (singular block)",
                     g.params_set == 1 ? "pg12_small" : "pg12_v1");
     g.params_ready = true;
+    return PG_OK;
+}
+
+// Constant tables of the active parameter set onto the current device: the
+// permutation constants of both permutation forms and the digit tables of
+// the tensor-core dense layers.
+pg_status upload_tables() {
+    dev::DevConsts dc;
+    dev::make_dev_consts(g.opt, dc);
+    PG_CUDA(cudaMemcpyToSymbol(dev::c_dev, &dc, sizeof(dc)));
+    PG_CUDA(cudaMemcpyToSymbol(dev::g_dev, &dc, sizeof(dc)));
+    static TcTables tt;  // 43 KB; built under g_mu
+    host::build_tc_tables(g.opt, tt);
+    PG_CUDA(cudaMemcpyToSymbol(dev::g_tc, &tt, sizeof(tt)));
     return PG_OK;
 }
 
@@ -731,6 +837,32 @@ cudaError_t launch_dependent(void (*kernel)(KArgs...), unsigned grid, unsigned b
     return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
 }
 
+// Tensor-core kernels: one CTA per SM at most, each CTA four 128-row units at a time.
+unsigned tc_grid(uint64_t n) {
+    const uint64_t units = (n + dev::kTcGroup - 1) / dev::kTcGroup;
+    const uint64_t want = (units + dev::kTcGroups - 1) / dev::kTcGroups;
+    return (unsigned)(want < (uint64_t)g.sms ? want : (uint64_t)g.sms);
+}
+
+pg_status launch_tc_sponge(const uint64_t *rows, uint64_t n, uint64_t w, uint64_t *out, cudaStream_t st, bool dependent,
+                           int kid) {
+    if (n == 0) return PG_OK;
+    const int vec16 = ((w % 2) == 0 && (reinterpret_cast<uintptr_t>(rows) % 16) == 0) ? 1 : 0;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(tc_grid(n));
+    cfg.blockDim = dim3(dev::kTcThreads);
+    cfg.dynamicSmemBytes = dev::TcL::kBytes;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = dependent ? 1 : 0;
+    ProfScope prof(kid, st, n * ((w + kRate - 1) / kRate));
+    PG_CUDA(cudaLaunchKernelEx(&cfg, dev::k_tc_sponge, rows, n, w, vec16, out));
+    return PG_OK;
+}
+
 pg_status launch_levels(uint64_t *nodes, uint64_t n_leaves, uint32_t first, cudaStream_t st) {
     const uint32_t log_n = log2u(n_leaves);
     for (uint32_t l = first; l <= log_n; ++l) {
@@ -741,7 +873,13 @@ pg_status launch_levels(uint64_t *nodes, uint64_t n_leaves, uint32_t first, cuda
             PG_CUDA(launch_dependent(dev::k_merkle_top_tail, dev::kTailCtas, dev::kTailBlock, st, nodes, n_leaves, l));
             break;
         }
-        if (cnt > kWideNodes) {
+        if (g.engine == 1 && cnt >= g.tc_min_nodes) {
+            // the level below, read as cnt rows of 8 words (children 2k, 2k+1)
+            const uint64_t *below = nodes + 4 * (2 * n_leaves - ((2 * n_leaves) >> (l - 1)));
+            uint64_t *here = nodes + 4 * (2 * n_leaves - ((2 * n_leaves) >> l));
+            pg_status s = launch_tc_sponge(below, cnt, 2 * kDigest, here, st, true, kIdTcLevel);
+            if (s != PG_OK) return s;
+        } else if (cnt > kWideNodes) {
             const uint64_t *below = nodes + 4 * (2 * n_leaves - ((2 * n_leaves) >> (l - 1)));
             uint64_t *here = nodes + 4 * (2 * n_leaves - ((2 * n_leaves) >> l));
             const unsigned grid = (unsigned)((cnt + 127) / 128);
@@ -761,6 +899,7 @@ pg_status launch_levels(uint64_t *nodes, uint64_t n_leaves, uint32_t first, cuda
 
 // Leaf digests of rows[0 .. n) on `st` (k_hash_rows, grid capped like pg_hash_rows).
 pg_status launch_leaves(const uint64_t *rows, uint64_t n, uint64_t width, uint64_t *digests, cudaStream_t st) {
+    if (g.engine == 1) return launch_tc_sponge(rows, n, width, digests, st, false, kIdTcRows);
     const int vec16 = ((width % 2) == 0 && (reinterpret_cast<uintptr_t>(rows) % 16) == 0) ? 1 : 0;
     const uint64_t want = (n + 127) / 128;
     const uint64_t cap = (uint64_t)g.sms * g.permute_blocks_per_sm * 8;
@@ -1169,15 +1308,44 @@ pg_status pg_params_select(const char *name) {
     if (s != PG_OK) return s;
     if (g.init) {
         PG_CUDA(cudaSetDevice(g.device));
-        dev::DevConsts dc;
-        dev::make_dev_consts(g.opt, dc);
-        PG_CUDA(cudaMemcpyToSymbol(dev::c_dev, &dc, sizeof(dc)));
-        PG_CUDA(cudaMemcpyToSymbol(dev::g_dev, &dc, sizeof(dc)));
+        s = upload_tables();
+        if (s != PG_OK) return s;
     }
     return PG_OK;
 }
 
 const char *pg_params_name(void) { return g.params_set == 1 ? "pg12_small" : "pg12_v1"; }
+
+size_t pg_tc_tables_export(void *out, size_t bytes) {
+    if (out == nullptr) return sizeof(TcTables);
+    if (bytes < sizeof(TcTables)) return 0;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (ensure_params() != PG_OK) return 0;
+    host::build_tc_tables(g.opt, *static_cast<TcTables *>(out));
+    return sizeof(TcTables);
+}
+
+pg_status pg_set_engine(int engine) {
+    if (engine != PG_ENGINE_INT && engine != PG_ENGINE_TENSOR)
+        return fail(PG_ERR_INVALID_ARG, "unknown engine %d (0: integer pipes, 1: tensor-core dense layers)", engine);
+    std::lock_guard<std::mutex> lk(g_mu);
+    g.engine = engine;
+    return PG_OK;
+}
+
+int pg_get_engine(void) { return g.engine; }
+
+pg_status pg_device_faults(uint32_t *faults) {
+    pg_status s = require_init();
+    if (s != PG_OK) return s;
+    if (!faults) return fail(PG_ERR_INVALID_ARG, "faults is NULL");
+    int v = 0;
+    const int zero = 0;
+    PG_CUDA(cudaMemcpyFromSymbol(&v, dev::g_tc_fault, sizeof v));
+    PG_CUDA(cudaMemcpyToSymbol(dev::g_tc_fault, &zero, sizeof zero));
+    *faults = (uint32_t)v;
+    return PG_OK;
+}
 
 pg_status pg_init(int device, const char *params_path) {
     {
@@ -1192,12 +1360,10 @@ pg_status pg_init(int device, const char *params_path) {
     PG_CUDA(cudaGetDeviceCount(&ndev));
     if (device < 0 || device >= ndev) return fail(PG_ERR_INVALID_ARG, "device %d out of range (%d)", device, ndev);
     PG_CUDA(cudaSetDevice(device));
-    {
-        dev::DevConsts dc;
-        dev::make_dev_consts(g.opt, dc);
-        PG_CUDA(cudaMemcpyToSymbol(dev::c_dev, &dc, sizeof(dc)));
-        PG_CUDA(cudaMemcpyToSymbol(dev::g_dev, &dc, sizeof(dc)));
-    }
+    s = upload_tables();
+    if (s != PG_OK) return s;
+    PG_CUDA(cudaFuncSetAttribute(dev::k_tc_permute, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dev::TcL::kBytes));
+    PG_CUDA(cudaFuncSetAttribute(dev::k_tc_sponge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dev::TcL::kBytes));
     {
         const int ns = ntt_upload_constants();
         if (ns != PG_OK) return (pg_status)ns;
@@ -1257,6 +1423,12 @@ pg_status pg_permute_batch(uint64_t *states, size_t n, void *stream) {
     if (!states) return fail(PG_ERR_INVALID_ARG, "states is NULL");
     if (reinterpret_cast<uintptr_t>(states) % 8) return fail(PG_ERR_INVALID_ARG, "states not 8-byte aligned");
     const int vec16 = (reinterpret_cast<uintptr_t>(states) % 16) == 0;
+    if (g.engine == 1) {
+        ProfScope prof(kIdTcPermute, as_stream(stream), (uint64_t)n);
+        dev::k_tc_permute<<<tc_grid(n), dev::kTcThreads, dev::TcL::kBytes, as_stream(stream)>>>(states, (uint64_t)n, vec16);
+        PG_CUDA(cudaGetLastError());
+        return PG_OK;
+    }
     const uint64_t want = (n + 127) / 128;
     const uint64_t cap = (uint64_t)g.sms * g.permute_blocks_per_sm * 8;
     const unsigned grid = (unsigned)(want < cap ? want : cap);
@@ -1275,6 +1447,7 @@ pg_status pg_hash_rows(const uint64_t *rows, size_t n_rows, size_t width, uint64
     if (!rows || !digests) return fail(PG_ERR_INVALID_ARG, "rows or digests is NULL");
     if (reinterpret_cast<uintptr_t>(rows) % 8) return fail(PG_ERR_INVALID_ARG, "rows not 8-byte aligned");
     if (reinterpret_cast<uintptr_t>(digests) % 16) return fail(PG_ERR_INVALID_ARG, "digests not 16-byte aligned");
+    if (g.engine == 1) return launch_tc_sponge(rows, n_rows, width, digests, as_stream(stream), false, kIdTcRows);
     const int vec16 = (width % 2 == 0) && (reinterpret_cast<uintptr_t>(rows) % 16) == 0;
     const uint64_t want = (n_rows + 127) / 128;
     const uint64_t cap = (uint64_t)g.sms * g.permute_blocks_per_sm * 8;
@@ -1325,6 +1498,11 @@ pg_status pg_merkle_build(const uint64_t *rows, size_t n_leaves, size_t width, u
         ProfScope prof(kIdMerkleTopLeaf, st, (uint64_t)n_leaves * ((width + kRate - 1) / kRate));
         dev::k_merkle_top_leaf<<<grid, dev::kTopBlock, 0, st>>>(rows, (uint64_t)n_leaves, (uint64_t)width, nodes);
         PG_CUDA(cudaGetLastError());
+    } else if (g.engine == 1) {
+        // leaf sponges on the tensor-core kernel (no plan, no counters)
+        first_top = 1;
+        s = launch_tc_sponge(rows, n_leaves, width, nodes, st, false, kIdTcLeaves);
+        if (s != PG_OK) return s;
     } else {
         PG_CUDA(cudaMemcpyAsync(d_plan, &tp, sizeof tp, cudaMemcpyHostToDevice, st));
         // the task counter, plus the arrival counters when the kernel climbs

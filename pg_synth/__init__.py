@@ -127,3 +127,49 @@ def words_torch(seed: int, count: int, start: int = 0, device="cpu", bound: int 
 
 def matrix_torch(seed: int, rows: int, cols: int, device="cpu", bound: int | None = FIELD_BOUND):
     return words_torch(seed, rows * cols, device=device, bound=bound).view(rows, cols)
+
+
+# ------------------------------------------------------------ workload recipes
+# Shapes and seeds of the benchmark workloads (no arithmetic of the method):
+# the bench, the tests and the script that stores the oracle's full-size
+# results all draw their inputs from here, so the stored values describe
+# exactly the inputs the GPU path is run on.
+
+def tree_rows_seed(log_n: int, width: int) -> int:
+    """Seed of the single-tree workloads (2^22 leaves x width 8 or 64)."""
+    return config_seed(3) if width == 8 else config_seed(3) + width
+
+
+def batch_sizes(trees: int = 64, max_log_n: int = 20, seed: int | None = None):
+    """(log2 leaves, width) of each tree of the batched workload: k log-uniform
+    in [12, min(20, max_log_n)], width uniform in {8, 16, 32, 64, 128}."""
+    seed = config_seed(4) if seed is None else seed
+    u = uniform01(seed, trees)
+    top = min(max_log_n, 20)
+    ks = [12 + int(v * (top - 12 + 1)) for v in u]
+    widths = [(8, 16, 32, 64, 128)[int(v)] for v in integers(seed + 1, trees, 0, 4)]
+    return [(min(k, top), w) for k, w in zip(ks, widths)]
+
+
+def batch_tree_seed(tree: int) -> int:
+    return tree_seed(config_seed(4), tree)
+
+
+SERVE_WIDTHS = (8, 32, 128, 256)
+
+
+def served_stream(requests: int = 2000, rate: float = 200.0, min_log_n: int = 10, max_log_n: int = 22,
+                  seed: int | None = None):
+    """Arrival times (s, Poisson at `rate`), log2 leaf counts (uniform in
+    [min_log_n, max_log_n]) and widths (uniform in SERVE_WIDTHS) of a served stream."""
+    seed = config_seed(5) if seed is None else seed
+    gaps = -np.log(1.0 - uniform01(seed, requests)) / rate
+    arrivals = np.cumsum(gaps)
+    ks = [int(k) for k in integers(seed + 1, requests, min_log_n, max_log_n)]
+    ws = [SERVE_WIDTHS[int(v)] for v in integers(seed + 2, requests, 0, len(SERVE_WIDTHS) - 1)]
+    return arrivals, ks, ws
+
+
+def served_rows_seed(log_n: int, width: int) -> int:
+    """Rows of every served request of shape (2^log_n leaves, width) come from this seed."""
+    return tree_seed(config_seed(5), (log_n << 16) | width)

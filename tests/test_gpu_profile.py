@@ -31,27 +31,37 @@ def _tree_perms(n, w):
     return n * ((w + 7) // 8) + n - 1
 
 
+@pytest.mark.parametrize("engine", [pg.ENGINE_TENSOR, pg.ENGINE_INT])
 @pytest.mark.parametrize("log_n,w", [(4, 8), (12, 3), (16, 8), (17, 20), (20, 8)])
-def test_build_launches_account_for_every_permutation(log_n, w):
+def test_build_launches_account_for_every_permutation(log_n, w, engine):
     rows = _rows(log_n, w, 0x7000 + log_n)
     nodes = torch.empty((2 * (1 << log_n) - 1, 4), dtype=torch.int64, device="cuda")
-    pg.profile_enable(True)
-    pg.merkle_build(rows, nodes)
-    pg.merkle_build(rows, nodes)
-    got = pg.profile_read()
-    pg.profile_enable(False)
+    pg.set_engine(engine)
+    try:
+        pg.profile_enable(True)
+        pg.merkle_build(rows, nodes)
+        pg.merkle_build(rows, nodes)
+        got = pg.profile_read()
+        pg.profile_enable(False)
+    finally:
+        pg.set_engine(pg.ENGINE_TENSOR)
     assert got.pop("_dropped") == 0
     assert sum(v["perms"] for v in got.values()) == 2 * _tree_perms(1 << log_n, w)
     assert all(v["total_ms"] > 0 for v in got.values())
     n = 1 << log_n
-    # the leaves in one launch (persistent kernel above 8,192 leaves, else the 16-lane
-    # kernel), then one launch per level: one thread per node (k_merkle_level) above 8,192
-    # nodes, else the 16-lane kernel (k_merkle_top)
+    tc = engine == pg.ENGINE_TENSOR
+    leaf_kernel = "k_tc_sponge:leaves" if tc else "k_merkle"
+    # the leaves in one launch (the persistent or tensor-core kernel above 8,192 leaves,
+    # else the 16-lane kernel), then one launch per level: the tensor-core kernel for
+    # levels of at least 2^15 nodes (tensor engine), one thread per node (k_merkle_level)
+    # above 8,192 nodes, else the 16-lane kernel (k_merkle_top)
     if n > 8192:
-        assert got["k_merkle"]["launches"] == 2 and got["k_merkle"]["perms"] == 2 * n * ((w + 7) // 8)
+        assert got[leaf_kernel]["launches"] == 2 and got[leaf_kernel]["perms"] == 2 * n * ((w + 7) // 8)
     else:
-        assert "k_merkle" not in got and got["k_merkle_top_leaf"]["launches"] == 2
-    per_node = sum(1 for l in range(1, log_n + 1) if n >> l > 8192)
+        assert leaf_kernel not in got and got["k_merkle_top_leaf"]["launches"] == 2
+    tc_levels = sum(1 for l in range(1, log_n + 1) if tc and n > 8192 and n >> l >= 1 << 15)
+    assert got.get("k_tc_sponge:level", {"launches": 0})["launches"] == 2 * tc_levels
+    per_node = sum(1 for l in range(1, log_n + 1) if n >> l > 8192) - tc_levels
     assert got.get("k_merkle_level", {"launches": 0})["launches"] == 2 * per_node
     # levels of 65..8,192 nodes: one k_merkle_top launch each; from the first level of at most
     # 64 nodes up to the root: one k_merkle_top_tail launch (or a lone root: k_merkle_top)
@@ -62,7 +72,7 @@ def test_build_launches_account_for_every_permutation(log_n, w):
         assert got.get("k_merkle_top", {"launches": 0})["launches"] == 2 * mid
     else:
         assert "k_merkle_top_tail" not in got
-        assert got.get("k_merkle_top", {"launches": 0})["launches"] == 2 * (log_n - per_node)
+        assert got.get("k_merkle_top", {"launches": 0})["launches"] == 2 * (log_n - per_node - tc_levels)
 
 
 def test_other_entry_points_are_recorded():
@@ -79,8 +89,8 @@ def test_other_entry_points_are_recorded():
     got = pg.profile_read()
     g.close()
     pg.profile_enable(False)
-    assert got["k_permute"] == {"launches": 1, "perms": 1000, "total_ms": got["k_permute"]["total_ms"]}
-    assert got["k_hash_rows"]["perms"] == 1024
+    assert got["k_tc_permute"] == {"launches": 1, "perms": 1000, "total_ms": got["k_tc_permute"]["total_ms"]}
+    assert got["k_tc_sponge:rows"]["perms"] == 1024
     batch = _tree_perms(1 << 9, 8) + _tree_perms(1 << 11, 16)
     # the batch launch and the graph launch (captured launches are not recorded)
     assert got["k_merkle"]["launches"] == 1 and got["k_merkle"]["perms"] == batch
