@@ -97,6 +97,12 @@ def parse_args():
     ap.add_argument("--max-log-n", type=int, default=22)
     ap.add_argument("--server-order", type=int, default=0, help="tree order inside a served batch: 0 arrival, 1 most work first")
     ap.add_argument("--params", default=None, help="built-in parameter set: pg12_v1 (default) or pg12_small")
+    ap.add_argument("--engine", choices=["tensor", "int"], default="tensor",
+                    help="permutation engine: tensor-core dense layers (default) or integer pipes only")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="skip the other workloads (permute, width-64 tree, batch, serve) of the default run")
+    ap.add_argument("--serve-low-rate", type=float, default=50.0)
+    ap.add_argument("--serve-low-requests", type=int, default=500)
     return ap.parse_args()
 
 
@@ -115,6 +121,38 @@ def measured_peaks():
             return json.load(f)
     except Exception:
         return {}
+
+
+# ------------------------------------------------------------ stored oracle results
+GOLDEN = os.path.join(ROOT, "tests", "golden", "full_size.json")
+
+
+def goldens() -> dict:
+    try:
+        with open(GOLDEN) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def sha256_words(t) -> str:
+    import hashlib
+    import numpy as np
+    a = t.detach().cpu().numpy() if not isinstance(t, np.ndarray) else t
+    return hashlib.sha256(np.ascontiguousarray(a).view(np.uint64).astype("<u8").tobytes()).hexdigest()
+
+
+def golden_tree(log_n, width, params=None):
+    """Stored oracle result of the single-tree workload of this shape, if any."""
+    if params not in (None, "pg12_v1"):
+        return None
+    return goldens().get(f"merkle_2e{log_n}_w{width}")
+
+
+def tree_matches(nodes, entry) -> bool:
+    import numpy as np
+    root = [int(v) for v in nodes[-1].cpu().numpy().view(np.uint64)]
+    return root == [int(v, 16) for v in entry["root"]] and sha256_words(nodes) == entry["nodes_sha256"]
 
 
 # ------------------------------------------------------------ clocks
@@ -295,10 +333,13 @@ def run_ours(args):
     torch.cuda.set_device(local)
     pg.load(build_if_missing=True)
     pg.init(local, args.params)
+    pg.set_engine(pg.ENGINE_TENSOR if args.engine == "tensor" else pg.ENGINE_INT)
     mul_per_perm = MUL_RESULTS_PER_PERM_SMALL if args.params == "pg12_small" else MUL_RESULTS_PER_PERM
 
     n, perms, name = workload(args.log_n, args.width)
-    rows_np = pg_synth.matrix(pg_synth.config_seed(3) + rank, n, args.width)
+    # every rank builds the same tree (replicas), from the seed whose oracle
+    # root and node-array hash are stored
+    rows_np = pg_synth.matrix(pg_synth.tree_rows_seed(args.log_n, args.width), n, args.width)
     rows = torch.from_numpy(rows_np.view(np.int64)).cuda()
     nodes = torch.empty((2 * n - 1, 4), dtype=torch.int64, device="cuda")
     stream = torch.cuda.current_stream()
@@ -454,6 +495,21 @@ def run_ours(args):
                         "share": v["total_ms"] / tot_kernel_ms} for k, v in kernels.items()},
         "clocks": clocks,
     }
+    # the timed tree against the oracle's stored result (when one is stored for this shape)
+    gold = golden_tree(args.log_n, args.width, args.params)
+    if gold is not None:
+        ok = tree_matches(nodes, gold)
+        if dist is not None:
+            t = torch.tensor([1 if ok else 0], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MIN)
+            ok = bool(t.item())
+        line["bit_exact"] = ok
+        line["bit_exact_basis"] = "root and SHA-256 of all 2N-1 nodes of the timed tree vs the stored oracle build"
+    else:
+        line["bit_exact"] = None
+    line["engine"] = "tensor" if pg.get_engine() == pg.ENGINE_TENSOR else "int"
+    if world == 1 and not args.headline_only:
+        line["workloads"] = run_sub_workloads(args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, cores, log_s, dt, sp = oracle_rate(args.width, args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate, "unit": "perms/s", "cores": cores, "kind": "oracle",
@@ -468,6 +524,11 @@ def run_ours(args):
 
 
 # ------------------------------------------------------------ other workloads
+# Each returns one dict: run alone with --workload, or embedded under
+# "workloads" in the default run's line.  Every one reports the device time,
+# permutations/s, the fraction of the IMAD roofline (algorithmic multiply
+# results at 64 per clock per SM), the clocks sampled while it ran, and
+# whether its outputs equal the oracle's stored results ("bit_exact").
 _ARGS = None
 
 
@@ -477,6 +538,8 @@ def _device_setup():
     torch.cuda.set_device(0)
     pg.load(build_if_missing=True)
     pg.init(0, _ARGS.params if _ARGS is not None else None)
+    if _ARGS is not None:
+        pg.set_engine(pg.ENGINE_TENSOR if _ARGS.engine == "tensor" else pg.ENGINE_INT)
     return torch, pg
 
 
@@ -487,29 +550,280 @@ def _peak_results_per_s():
     return IMAD_RESULTS_PER_CLK_SM * sms * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
 
 
-def run_permute(args):
-    """2^24 independent states permuted in place (raw permutation throughput)."""
+def _mul_per_perm(args):
+    return MUL_RESULTS_PER_PERM_SMALL if args.params == "pg12_small" else MUL_RESULTS_PER_PERM
+
+
+def _imad_frac(args, perms, seconds):
+    return perms * _mul_per_perm(args) / seconds / _peak_results_per_s()
+
+
+def _gpu_id():
+    import torch
+    try:
+        u = str(torch.cuda.get_device_properties(0).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return None
+
+
+def _timed(fn, steps, warmup):
+    """Device ms per call of fn() (CUDA events on the current stream, after warm-up),
+    with the GPU clocks sampled during the timed calls."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(_gpu_id())
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    return e0.elapsed_time(e1) / steps, clocks
+
+
+def measure_permute(args):
+    """Workload 2: 2^24 independent states permuted in place (raw permutation throughput)."""
     torch, pg = _device_setup()
     import pg_synth
     n = 1 << 24
-    st = pg_synth.matrix_torch(pg_synth.config_seed(2), n, 12, device="cuda")
-    for _ in range(args.warmup):
-        pg.permute_batch(st)
+    seed = pg_synth.config_seed(2)
+    st = pg_synth.matrix_torch(seed, n, 12, device="cuda")
+    # one permutation of the seeded states, checked against the stored oracle output
+    pg.permute_batch(st)
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(args.steps):
-        pg.permute_batch(st)
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
+    g = goldens().get("permute_2e24")
+    exact = (sha256_words(st) == g["states_sha256"]) if g and args.params in (None, "pg12_v1") else None
+    ms, clocks = _timed(lambda: pg.permute_batch(st), args.steps, args.warmup)
     rate = n / (ms / 1e3)
-    ach = rate * (MUL_RESULTS_PER_PERM_SMALL if args.params == "pg12_small" else MUL_RESULTS_PER_PERM)
-    line = {"workload": "permute 2^24 states in place", "params": args.params or "pg12_v1",
-            "metric": "perms/s", "value": rate,
-            "ms_per_step": ms, "steps": args.steps, "kernel": "k_permute",
-            "roofline": {"bound": "alu", "achieved": ach / 1e12, "peak": _peak_results_per_s() / 1e12,
-                         "unit": "T mul32-results/s", "frac": ach / _peak_results_per_s()}}
+    out = {"workload": "permute 2^24 states in place", "params": args.params or "pg12_v1",
+           "ms": ms, "perms_per_s": rate, "imad_frac": _imad_frac(args, n, ms / 1e3),
+           "kernel": "k_tc_permute" if pg.get_engine() == pg.ENGINE_TENSOR else "k_permute",
+           "bit_exact": exact, "bit_exact_basis": "SHA-256 of the 2^24 states after one permutation vs the oracle's",
+           "clocks": clocks}
+    del st
+    torch.cuda.empty_cache()
+    return out
+
+
+def measure_tree(args, log_n, width):
+    """Workload 3: one tree of 2^log_n leaves of `width` words (rows resident in HBM)."""
+    torch, pg = _device_setup()
+    import pg_synth
+    n, perms, name = workload(log_n, width)
+    rows = pg_synth.matrix_torch(pg_synth.tree_rows_seed(log_n, width), n, width, device="cuda")
+    nodes = torch.empty((2 * n - 1, 4), dtype=torch.int64, device="cuda")
+    ms, clocks = _timed(lambda: pg.merkle_build(rows, nodes), args.steps, args.warmup)
+    g = golden_tree(log_n, width, args.params)
+    out = {"workload": name, "ms": ms, "perms_per_s": perms / (ms / 1e3),
+           "imad_frac": _imad_frac(args, perms, ms / 1e3),
+           "bit_exact": tree_matches(nodes, g) if g else None, "clocks": clocks}
+    del rows, nodes
+    torch.cuda.empty_cache()
+    return out
+
+
+def measure_batch(args):
+    """Workload 4: 64 trees of mixed sizes and widths in one captured persistent launch
+    (autotuned schedule) against one pg_merkle_build per tree, same GPU, same inputs."""
+    torch, pg = _device_setup()
+    import pg_synth
+    sizes = pg_synth.batch_sizes(args.trees, args.max_log_n)
+    rows = [pg_synth.matrix_torch(pg_synth.batch_tree_seed(k), 1 << lg, w, device="cuda")
+            for k, (lg, w) in enumerate(sizes)]
+    perms = sum((1 << lg) * ((w + 7) // 8) + (1 << lg) - 1 for lg, w in sizes)
+    nodes = pg.alloc_nodes(rows)
+    t0 = time.perf_counter()
+    best, tune_ms = pg.batch_autotune(rows, nodes)
+    tune_s = time.perf_counter() - t0
+    g = pg.BatchGraph(rows, nodes, schedule=best)
+    ms_batch, clocks = _timed(g.launch, args.steps, args.warmup)
+    gold = goldens()
+    exact = None
+    if args.trees == 64 and args.max_log_n >= 20 and args.params in (None, "pg12_v1"):
+        exact = all(sha256_words(nd) == gold[f"batch_{k:02d}"]["nodes_sha256"] for k, nd in enumerate(nodes)) \
+            if all(f"batch_{k:02d}" in gold for k in range(64)) else None
+    batch_out = [t.clone() for t in nodes]
+    g.close()
+    single = [torch.empty_like(t) for t in nodes]
+
+    def one_per_tree():
+        for r, nd in zip(rows, single):
+            pg.merkle_build(r, nd)
+    ms_single, clocks_single = _timed(one_per_tree, args.steps, args.warmup)
+    same = all(torch.equal(a, b) for a, b in zip(batch_out, single))
+    out = {
+        "workload": f"batch of {len(sizes)} trees, 2^k leaves k in [12,20], widths in {{8..128}}",
+        "perms_per_step": perms, "trees": [[lg, w] for lg, w in sizes],
+        "batched_graph": {"ms": ms_batch, "perms_per_s": perms / (ms_batch / 1e3),
+                          "imad_frac": _imad_frac(args, perms, ms_batch / 1e3),
+                          "schedule": best, "autotune_best_ms": tune_ms, "autotune_s": tune_s, "clocks": clocks},
+        "one_launch_per_tree": {"ms": ms_single, "perms_per_s": perms / (ms_single / 1e3),
+                                "imad_frac": _imad_frac(args, perms, ms_single / 1e3), "clocks": clocks_single},
+        "speedup": ms_single / ms_batch, "bit_identical_to_single": same, "bit_exact": exact,
+        "bit_exact_basis": "SHA-256 of every tree's 2N-1 nodes from the captured launch vs the stored oracle builds",
+    }
+    del rows, nodes, single, batch_out
+    torch.cuda.empty_cache()
+    return out
+
+
+def _serve_stream(args, requests, rate):
+    import pg_synth
+    arrivals, ks, ws = pg_synth.served_stream(requests, rate, 10, args.max_log_n)
+    perms = [(1 << k) * ((w + 7) // 8) + (1 << k) - 1 for k, w in zip(ks, ws)]
+    return arrivals, ks, ws, perms
+
+
+def _serve_rows(torch, shapes):
+    import pg_synth
+    # payloads are materialised on the device ahead of their arrival (not timed);
+    # every request of one (k, w) shape reuses that shape's rows
+    return {key: pg_synth.matrix_torch(pg_synth.served_rows_seed(*key), 1 << key[0], key[1], device="cuda")
+            for key in sorted(set(shapes))}
+
+
+def _serve_server(torch, pg, args, arrivals, ks, ws, cache, keep_shapes=()):
+    """The serving runtime on an arrival trace: per-request latency (arrival -> root
+    stored), makespan, and copies of the first result of each shape in keep_shapes."""
+    import numpy as np
+    pool = int(min(torch.cuda.mem_get_info()[0] * 0.5, 64 << 30))
+    srv = pg.Server(pool_bytes=pool, max_batch=256, max_inflight=2, schedule={"order": args.server_order})
+    lat, pending, kept = {}, [], {}
+    keep = {k: torch.empty((2 * (1 << k[0]) - 1, 4), dtype=torch.int64, device="cuda") for k in keep_shapes}
+    shape_of = {}
+
+    def reap():
+        rest = []
+        for rid in pending:
+            info = srv.query(rid)
+            if info["state"] in (pg.REQ_DONE, pg.REQ_FAILED):
+                if info["state"] != pg.REQ_DONE:
+                    raise RuntimeError(f"request {rid} failed")
+                lat[rid] = info["done_s"] - info["submit_s"]
+                key = shape_of[rid]
+                if key in keep and key not in kept:
+                    keep[key].copy_(srv.nodes(rid, 1 << key[0]))
+                    kept[key] = True
+                srv.release(rid)
+            else:
+                rest.append(rid)
+        pending[:] = rest
+
+    t_start = time.perf_counter()
+    for i in range(len(arrivals)):
+        while True:
+            now = time.perf_counter() - t_start
+            if arrivals[i] <= now:
+                break
+            reap()
+            now = time.perf_counter() - t_start
+            if arrivals[i] > now:
+                time.sleep(min(arrivals[i] - now, 0.002))
+        key = (ks[i], ws[i])
+        rid = srv.submit(cache[key])
+        shape_of[rid] = key
+        pending.append(rid)
+    while pending:
+        reap()
+        time.sleep(0.001)
+        if time.perf_counter() - t_start > 900:
+            raise RuntimeError("serving run did not finish")
+    t_end = time.perf_counter() - t_start
+    srv.close()
+    torch.cuda.synchronize()
+    return np.array(list(lat.values())), t_end, keep
+
+
+def _serve_sequential(torch, pg, arrivals, ks, ws, cache):
+    """Measured baseline: one pg_merkle_build per request, launched in arrival order on
+    one stream as each request arrives; latency = arrival -> the build's completion
+    event (times on the device's clock, from an event recorded at the trace's start)."""
+    import numpy as np
+    nodes = {key: torch.empty((2 * r.shape[0] - 1, 4), dtype=torch.int64, device="cuda") for key, r in cache.items()}
+    done = [torch.cuda.Event(enable_timing=True) for _ in range(len(arrivals))]
+    start = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    start.record()
+    t_start = time.perf_counter()
+    for i in range(len(arrivals)):
+        while time.perf_counter() - t_start < arrivals[i]:
+            time.sleep(0.0002)
+        key = (ks[i], ws[i])
+        pg.merkle_build(cache[key], nodes[key])
+        done[i].record()
+    torch.cuda.synchronize()
+    fin = np.array([start.elapsed_time(e) / 1e3 for e in done])
+    return fin - np.asarray(arrivals), float(fin.max())
+
+
+def measure_serve(args):
+    """Workload 5: Poisson stream of tree builds through the serving runtime against
+    sequential single-tree builds on the same trace, at the workload's rate (over the
+    GPU's capacity) and at a rate under it."""
+    torch, pg = _device_setup()
+    import numpy as np
+    gold = goldens()
+    peak = _peak_results_per_s()
+    out = {}
+    for label, nreq, rate in (("rate_200", args.requests, args.rate),
+                              ("rate_low", args.serve_low_requests, args.serve_low_rate)):
+        arrivals, ks, ws, perms = _serve_stream(args, nreq, rate)
+        cache = _serve_rows(torch, list(zip(ks, ws)))
+        torch.cuda.synchronize()
+        keep_shapes = [s for s in ((22, 8), (22, 32)) if s in cache] if label == "rate_200" else []
+        sampler = ClockSampler(_gpu_id())
+        lat, makespan, kept = _serve_server(torch, pg, args, arrivals, ks, ws, cache, keep_shapes)
+        clocks = sampler.stop()
+        seq_lat, seq_makespan = _serve_sequential(torch, pg, arrivals, ks, ws, cache)
+        total = int(sum(perms))
+        exact = None
+        if keep_shapes and args.params in (None, "pg12_v1"):
+            exact = all(tree_matches(kept[s], gold[f"serve_2e22_w{s[1]}"]) for s in keep_shapes
+                        if f"serve_2e22_w{s[1]}" in gold)
+        out[label] = {
+            "requests": nreq, "rate_per_s": rate, "total_perms": total,
+            "offered_perms_per_s": total / float(arrivals[-1]),
+            "server": {"makespan_s": makespan, "perms_per_s": total / makespan,
+                       "imad_frac": total * _mul_per_perm(args) / makespan / peak,
+                       "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+                       "clocks": clocks},
+            "sequential_builds": {"makespan_s": seq_makespan, "perms_per_s": total / seq_makespan,
+                                  "imad_frac": total * _mul_per_perm(args) / seq_makespan / peak,
+                                  "p50_latency_s": float(np.percentile(seq_lat, 50)),
+                                  "p99_latency_s": float(np.percentile(seq_lat, 99))},
+            "bit_exact": exact,
+        }
+        if keep_shapes:
+            out[label]["bit_exact_basis"] = ("first served 2^22-leaf result of widths " +
+                                             ", ".join(str(s[1]) for s in keep_shapes) +
+                                             ": root and SHA-256 of all nodes vs the stored oracle builds")
+        del cache, kept
+        torch.cuda.empty_cache()
+    out["workload"] = (f"serve Poisson requests, 2^k leaves k in [10,{args.max_log_n}], widths {{8,32,128,256}}: "
+                       f"{args.requests} at {args.rate}/s and {args.serve_low_requests} at {args.serve_low_rate}/s")
+    return out
+
+
+def run_sub_workloads(args):
+    """The other configurations, each measured in this run (workloads 2, 3b, 4, 5)."""
+    out = {}
+    steps = max(3, min(args.steps, 10))
+    sub = argparse.Namespace(**vars(args))
+    sub.steps = steps
+    out["permute"] = measure_permute(sub)
+    out["merkle_w64"] = measure_tree(sub, 22, 64)
+    out["batch"] = measure_batch(sub)
+    out["serve"] = measure_serve(sub)
+    return out
+
+
+def run_permute(args):
+    line = measure_permute(args)
     if not args.no_cpu_baseline and not args.params:
         rates = oracle_permute_rates()
         line["cpu_baseline"] = {"value": rates["all_core"]["perms_per_s"], "unit": "perms/s",
@@ -521,158 +835,13 @@ def run_permute(args):
     return 0
 
 
-def _batch_sizes(seed, trees, max_log_n):
-    import pg_synth
-    u = pg_synth.uniform01(seed, trees)
-    ks = [12 + int(v * (min(max_log_n, 20) - 12 + 1)) for v in u]
-    widths = [(8, 16, 32, 64, 128)[int(v)] for v in pg_synth.integers(seed + 1, trees, 0, 4)]
-    return [(min(k, 20), w) for k, w in zip(ks, widths)]
-
-
 def run_batch(args):
-    """64 trees of mixed sizes and widths: one captured persistent launch (autotuned
-    schedule) against one pg_merkle_build launch per tree, same GPU, same inputs."""
-    torch, pg = _device_setup()
-    import pg_synth
-    sizes = _batch_sizes(pg_synth.config_seed(4), args.trees, args.max_log_n)
-    rows = [pg_synth.matrix_torch(pg_synth.tree_seed(pg_synth.config_seed(4), k), 1 << lg, w, device="cuda")
-            for k, (lg, w) in enumerate(sizes)]
-    perms = sum((1 << lg) * ((w + 7) // 8) + (1 << lg) - 1 for lg, w in sizes)
-    nodes = pg.alloc_nodes(rows)
-    best, tune_ms = pg.batch_autotune(rows, nodes)
-    g = pg.BatchGraph(rows, nodes, schedule=best)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    for _ in range(args.warmup):
-        g.launch()
-    torch.cuda.synchronize()
-    e0.record()
-    for _ in range(args.steps):
-        g.launch()
-    e1.record()
-    torch.cuda.synchronize()
-    ms_batch = e0.elapsed_time(e1) / args.steps
-    batch_out = [t.clone() for t in nodes]
-    single = [torch.empty_like(t) for t in nodes]
-    for _ in range(args.warmup):
-        for r, nd in zip(rows, single):
-            pg.merkle_build(r, nd)
-    torch.cuda.synchronize()
-    e0.record()
-    for _ in range(args.steps):
-        for r, nd in zip(rows, single):
-            pg.merkle_build(r, nd)
-    e1.record()
-    torch.cuda.synchronize()
-    ms_single = e0.elapsed_time(e1) / args.steps
-    same = all(torch.equal(a, b) for a, b in zip(batch_out, single))
-    g.close()
-    peak = _peak_results_per_s()
-    print(json.dumps({
-        "workload": f"batch of {len(sizes)} trees, 2^k leaves k in [12,20], widths in {{8..128}}",
-        "perms_per_step": perms, "trees": [[lg, w] for lg, w in sizes],
-        "batched_graph": {"ms": ms_batch, "perms_per_s": perms / (ms_batch / 1e3),
-                          "imad_frac": perms * MUL_RESULTS_PER_PERM / (ms_batch / 1e3) / peak,
-                          "schedule": best, "autotune_best_ms": tune_ms},
-        "one_launch_per_tree": {"ms": ms_single, "perms_per_s": perms / (ms_single / 1e3),
-                                "imad_frac": perms * MUL_RESULTS_PER_PERM / (ms_single / 1e3) / peak},
-        "speedup": ms_single / ms_batch, "bit_identical": same}), flush=True)
+    print(json.dumps(measure_batch(args)), flush=True)
     return 0
 
 
 def run_serve(args):
-    """Poisson stream of tree builds through the serving runtime against a
-    sequential FIFO of single-tree builds on the same arrival trace."""
-    torch, pg = _device_setup()
-    import numpy as np
-    import pg_synth
-    seed = pg_synth.config_seed(5)
-    nreq = args.requests
-    gaps = -np.log(1.0 - pg_synth.uniform01(seed, nreq)) / args.rate
-    arrivals = np.cumsum(gaps)
-    ks = pg_synth.integers(seed + 1, nreq, 10, args.max_log_n)
-    ws = [(8, 32, 128, 256)[int(v)] for v in pg_synth.integers(seed + 2, nreq, 0, 3)]
-    perms = [int((1 << int(k)) * ((w + 7) // 8) + (1 << int(k)) - 1) for k, w in zip(ks, ws)]
-    # payloads are materialised on the device ahead of their arrival (not timed); to bound
-    # memory, requests reuse a small set of row buffers generated per (k, w) shape
-    cache = {}
-
-    def rows_for(i):
-        key = (int(ks[i]), ws[i])
-        if key not in cache:
-            cache[key] = pg_synth.matrix_torch(pg_synth.tree_seed(seed, len(cache)), 1 << key[0], key[1], device="cuda")
-        return cache[key]
-
-    for i in range(nreq):
-        rows_for(i)
-    torch.cuda.synchronize()
-    pool = int(min(torch.cuda.mem_get_info()[0] * 0.5, 64 << 30))
-    srv = pg.Server(pool_bytes=pool, max_batch=256, max_inflight=2, schedule={"order": args.server_order})
-    import time as _t
-    lat = {}
-    pending = []
-
-    def reap():
-        keep = []
-        for rid in pending:
-            info = srv.query(rid)
-            if info["state"] in (pg.REQ_DONE, pg.REQ_FAILED):
-                if info["state"] != pg.REQ_DONE:
-                    raise RuntimeError(f"request {rid} failed")
-                lat[rid] = info["done_s"] - info["submit_s"]
-                srv.release(rid)
-            else:
-                keep.append(rid)
-        pending[:] = keep
-
-    t_start = _t.perf_counter()
-    for i in range(nreq):
-        while True:
-            now = _t.perf_counter() - t_start
-            if arrivals[i] <= now:
-                break
-            reap()
-            now = _t.perf_counter() - t_start
-            if arrivals[i] > now:
-                _t.sleep(min(arrivals[i] - now, 0.002))
-        pending.append(srv.submit(rows_for(i)))
-    while pending:
-        reap()
-        _t.sleep(0.001)
-        if _t.perf_counter() - t_start > 900:
-            raise RuntimeError("serving run did not finish")
-    t_end = _t.perf_counter() - t_start
-    srv.close()
-    lat = list(lat.values())
-    lat = np.array(lat)
-    total_perms = sum(perms)
-    # sequential FIFO: one pg_merkle_build per request in arrival order, each
-    # starting at max(arrival, previous finish); device time per build measured
-    times = {}
-    for key, r in cache.items():
-        nd = torch.empty((2 * r.shape[0] - 1, 4), dtype=torch.int64, device="cuda")
-        pg.merkle_build(r, nd)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(3):
-            pg.merkle_build(r, nd)
-        e1.record()
-        torch.cuda.synchronize()
-        times[key] = e0.elapsed_time(e1) / 3 / 1e3
-    fin, seq_lat = 0.0, []
-    for i in range(nreq):
-        start = max(arrivals[i], fin)
-        fin = start + times[(int(ks[i]), ws[i])]
-        seq_lat.append(fin - arrivals[i])
-    seq_lat = np.array(seq_lat)
-    print(json.dumps({
-        "workload": f"serve {nreq} Poisson requests at {args.rate}/s, 2^k leaves k in [10,{args.max_log_n}], widths {{8,32,128,256}}",
-        "total_perms": total_perms,
-        "server": {"makespan_s": t_end, "perms_per_s": total_perms / t_end,
-                   "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99))},
-        "sequential_fifo": {"makespan_s": float(fin), "perms_per_s": total_perms / fin,
-                            "p50_latency_s": float(np.percentile(seq_lat, 50)),
-                            "p99_latency_s": float(np.percentile(seq_lat, 99))},
-        "offered_perms_per_s": total_perms / float(arrivals[-1])}), flush=True)
+    print(json.dumps(measure_serve(args)), flush=True)
     return 0
 
 

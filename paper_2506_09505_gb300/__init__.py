@@ -278,6 +278,17 @@ def hash_rows(rows, digests=None, stream=None):
     return digests
 
 
+def _check_nodes(nodes, n: int, rows) -> None:
+    """A caller-supplied node buffer must hold the whole tree on the rows' GPU:
+    the kernels write (2N-1) x 4 words into it and cannot check its size."""
+    need = 4 * (2 * n - 1) if n > 0 else 0
+    if nodes.numel() < need:
+        raise ValueError(f"nodes holds {nodes.numel()} words; a tree of {n} leaves needs {need}")
+    if nodes.device != rows.device:
+        raise ValueError(f"nodes is on {nodes.device}, rows on {rows.device}")
+    _dev_ptr(nodes, "nodes")
+
+
 def merkle_build(rows, nodes=None, want_root: bool = False, stream=None):
     """Whole tree over a (N, w) CUDA tensor -> nodes (2N-1, 4), level-major.
 
@@ -290,6 +301,8 @@ def merkle_build(rows, nodes=None, want_root: bool = False, stream=None):
     n, w = rows.shape
     if nodes is None:
         nodes = torch.empty((max(2 * n - 1, 1), DIGEST), dtype=rows.dtype, device=rows.device)
+    else:
+        _check_nodes(nodes, n, rows)
     root = (ctypes.c_uint64 * 4)() if want_root else None
     _check(load().pg_merkle_build(_dev_ptr(rows, "rows"), n, w, _dev_ptr(nodes, "nodes"),
                                   ctypes.cast(root, _u64p) if want_root else None,
@@ -333,6 +346,7 @@ def merkle_build_noalloc(rows, nodes, stream=None):
     if rows.dim() != 2:
         raise ValueError("rows must have shape (N, w)")
     n, w = rows.shape
+    _check_nodes(nodes, n, rows)
     _check(load().pg_merkle_build_noalloc(_dev_ptr(rows, "rows"), n, w, _dev_ptr(nodes, "nodes"),
                                           _stream(stream)))
     return nodes

@@ -61,3 +61,31 @@ def test_profile_store_empty_on_host(lib):
     got = pg.profile_read()
     pg.profile_enable(False)
     assert got == {"_dropped": 0}
+
+
+def test_undersized_node_buffers_are_refused_before_any_launch():
+    # the kernels write (2N-1) x 4 words and cannot check the buffer, so the
+    # binding refuses a short one (or one on another device) before calling
+    # the library
+    torch = pytest.importorskip("torch")
+    rows = torch.zeros((1 << 10, 8), dtype=torch.int64)
+    short = torch.zeros((2 * (1 << 10) - 2, 4), dtype=torch.int64)
+    with pytest.raises(ValueError, match="needs"):
+        pg.merkle_build_noalloc(rows, short)
+    with pytest.raises(ValueError, match="needs"):
+        pg.merkle_build(rows, short)
+    meta = torch.zeros((2 * (1 << 10) - 1, 4), dtype=torch.int64, device="meta")
+    with pytest.raises(ValueError, match="meta"):
+        pg.merkle_build_noalloc(rows, meta)
+
+
+def test_engine_switch_is_validated(lib):
+    assert pg.get_engine() in (pg.ENGINE_INT, pg.ENGINE_TENSOR)
+    before = pg.get_engine()
+    pg.set_engine(pg.ENGINE_INT)
+    assert pg.get_engine() == pg.ENGINE_INT
+    pg.set_engine(before)
+    with pytest.raises(pg.PGError) as e:
+        pg.set_engine(7)
+    assert e.value.status == 1
+    assert pg.get_engine() == before

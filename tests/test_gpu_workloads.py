@@ -20,7 +20,6 @@ from tree_check import check_tree_sampled
 
 torch = pytest.importorskip("torch")
 pg = pytest.importorskip("paper_2506_09505_gb300")
-bench = pytest.importorskip("bench")
 
 pytestmark = pytest.mark.gpu
 
@@ -38,9 +37,8 @@ def _host(t):
 
 
 def test_batch_workload_distribution():
-    seed = pg_synth.config_seed(4)
-    sizes = bench._batch_sizes(seed, 64, 20)
-    rows = [pg_synth.matrix_torch(pg_synth.tree_seed(seed, k), 1 << lg, w, device="cuda")
+    sizes = pg_synth.batch_sizes(64, 20)
+    rows = [pg_synth.matrix_torch(pg_synth.batch_tree_seed(k), 1 << lg, w, device="cuda")
             for k, (lg, w) in enumerate(sizes)]
     nodes = pg.alloc_nodes(rows)
     best, _ = pg.batch_autotune(rows, nodes)
