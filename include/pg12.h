@@ -57,17 +57,35 @@ typedef struct {
     uint64_t *nodes;      /* dev, (2*n_leaves-1)*4 words, level-major output  */
 } pg_tree;
 
-/* Launch schedule of the persistent Merkle kernel.  Zero fields take the
- * defaults.  One thread owns one state, a warp hashes 32 nodes of one level
- * per task, and no levels are fused per block (upper levels are separate
- * warp tasks), so the tunables are the block size, how many blocks of the
- * persistent grid sit on each SM, and the order in which trees hand out
- * their leaf tasks. */
+/* Launch schedule of a batch (pg_merkle_build_batch, pg_batch_graph_create,
+ * the server).  Zero fields take the defaults.  Three knobs shape the work:
+ *   engine       the persistent kernel: tensor-core groups (128 threads
+ *                own 128 states; tasks are units of 128 nodes of one level)
+ *                or integer pipes (one thread per state; tasks are 32 nodes
+ *                hashed by one warp).
+ *   fuse_levels  tensor engine: levels a task builds on its own.  A task is
+ *                2^f consecutive leaf units (2^f * 128 leaves); its group
+ *                also builds the f levels above them before it meets other
+ *                tasks through arrival counters (the second of two sibling
+ *                units to finish builds their parent unit).
+ *   top_lanes    threads per state of a tree's top levels: 1 = the
+ *                persistent kernel climbs every tree to its root; 16 = it
+ *                stops below the first level of at most 64 nodes, and a
+ *                second launch builds every tree's remaining levels with 16
+ *                lanes per node (one block per tree, latency form).
+ * plus, for the integer engine, the block size and persistent blocks per
+ * SM, and for both the order in which trees hand out their leaf tasks. */
+#define PG_BATCH_ENGINE_DEFAULT 0 /* the process's engine (pg_get_engine) */
+#define PG_BATCH_ENGINE_INT 1
+#define PG_BATCH_ENGINE_TENSOR 2
 typedef struct {
-    uint32_t block;         /* threads per block: 128 or 256 (default 256)        */
-    uint32_t blocks_per_sm; /* persistent blocks per SM, capped by occupancy      */
-    uint32_t order;         /* 0 = trees as given, 1 = most work first (default 0) */
-    uint32_t reserved;      /* must be 0                                           */
+    uint32_t block;         /* integer engine: threads per block, 128 or 256 (default 256)  */
+    uint32_t blocks_per_sm; /* integer engine: persistent blocks per SM, capped by occupancy */
+    uint32_t order;         /* 0 = trees as given, 1 = most work first (default 0)          */
+    uint32_t engine;        /* PG_BATCH_ENGINE_*                                           */
+    uint32_t fuse_levels;   /* tensor engine: 0..3 (default 0)                             */
+    uint32_t top_lanes;     /* 0 or 1 = climb to the roots (default), 16 = hand off         */
+    uint32_t reserved[2];   /* must be 0                                                   */
 } pg_schedule;
 
 /* Opaque handle of a captured batch (see pg_batch_graph_create). */
@@ -163,6 +181,12 @@ const char *pg_params_name(void);
  * pg_set_engine applies to launches made after it returns; PG_ERR_INVALID_ARG
  * for any other value.  Host-only.
  */
+
+#define PG_ENGINE_INT 0
+#define PG_ENGINE_TENSOR 1
+pg_status pg_set_engine(int engine);
+int pg_get_engine(void);
+
 /*
  * pg_tc_tables_export -- host copy of the tensor-core digit tables of the
  * active parameter set, for inspection and CPU tests: with out == NULL
@@ -179,11 +203,6 @@ const char *pg_params_name(void);
  * Host-only; works without a GPU.
  */
 size_t pg_tc_tables_export(void *out, size_t bytes);
-
-#define PG_ENGINE_INT 0
-#define PG_ENGINE_TENSOR 1
-pg_status pg_set_engine(int engine);
-int pg_get_engine(void);
 
 /*
  * pg_device_faults -- *faults = 1 if a tensor-core kernel launched since the
@@ -306,9 +325,11 @@ pg_status pg_merkle_build_host(const uint64_t *rows_host, size_t n_leaves, size_
 /*
  * pg_merkle_build_batch -- Sec. 4.2 trees of mixed sizes and widths built
  * in ONE persistent launch: leaf tasks of all trees come from one counter
- * and each tree's upper levels are built by the warp that completes the
- * second child task, so small trees' top levels overlap with other trees'
- * leaf work.  Results are identical to pg_merkle_build on each tree alone.
+ * and each tree's upper levels are built by the group (tensor engine) or
+ * warp (integer engine) that completes the second of two sibling tasks, so
+ * small trees' top levels overlap with other trees' leaf work; with
+ * top_lanes = 16 a second launch builds the levels of at most 64 nodes.
+ * Results are identical to pg_merkle_build on each tree alone.
  *   trees    host array of n_trees descriptors (device buffers, caller-owned;
  *            node buffers of different trees must not overlap).
  *   n_trees  >= 1.
@@ -335,9 +356,11 @@ pg_status pg_batch_graph_launch(pg_batch_graph *graph, void *stream);
 pg_status pg_batch_graph_destroy(pg_batch_graph *graph);
 
 /*
- * pg_batch_autotune -- time each candidate schedule (block 128/256 x
- * persistent blocks per SM x tree order) on the real batch with CUDA events
- * and return the fastest in *best (and its time in *best_ms if non-NULL).
+ * pg_batch_autotune -- time each candidate schedule on the real batch with
+ * CUDA events and return the fastest in *best (and its time in *best_ms if
+ * non-NULL).  Candidates: tensor engine x tree order {given, most work
+ * first} x levels fused per task {0, 1, 2} x top-level lanes {1, 16}, and
+ * integer engine x order x block {256, 128} x top-level lanes {1, 16}.
  * Runs the batch several times on `stream` (outputs are overwritten with the
  * same values); synchronous.
  */

@@ -48,10 +48,25 @@ class Tree(ctypes.Structure):
 class Schedule(ctypes.Structure):
     """pg_schedule of include/pg12.h."""
     _fields_ = [("block", ctypes.c_uint32), ("blocks_per_sm", ctypes.c_uint32), ("order", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32)]
+                ("engine", ctypes.c_uint32), ("fuse_levels", ctypes.c_uint32), ("top_lanes", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 2)]
+
+    KEYS = ("block", "blocks_per_sm", "order", "engine", "fuse_levels", "top_lanes")
 
     def as_dict(self):
-        return {"block": self.block, "blocks_per_sm": self.blocks_per_sm, "order": self.order}
+        return {k: int(getattr(self, k)) for k in self.KEYS}
+
+    @classmethod
+    def of(cls, d):
+        sc = cls()
+        for k, v in (d or {}).items():
+            if k not in cls.KEYS:
+                raise ValueError(f"unknown schedule field {k!r}")
+            setattr(sc, k, int(v))
+        return sc
+
+
+BATCH_ENGINE_DEFAULT, BATCH_ENGINE_INT, BATCH_ENGINE_TENSOR = 0, 1, 2
 
 class ServerConfig(ctypes.Structure):
     """pg_server_config of include/pg12.h."""
@@ -369,8 +384,7 @@ def _sched(schedule):
         return None
     if isinstance(schedule, Schedule):
         return ctypes.byref(schedule)
-    sc = Schedule(schedule.get("block", 0), schedule.get("blocks_per_sm", 0), schedule.get("order", 0), 0)
-    return ctypes.byref(sc)
+    return ctypes.byref(Schedule.of(schedule))
 
 
 def alloc_nodes(rows_list):
@@ -529,11 +543,7 @@ class Server:
     """Continuous-batching tree-build server (pg_server_* of include/pg12.h)."""
 
     def __init__(self, pool_bytes=0, max_batch=0, max_inflight=0, schedule=None):
-        sc = Schedule()
-        if schedule:
-            sc.block, sc.blocks_per_sm, sc.order = (schedule.get("block", 0), schedule.get("blocks_per_sm", 0),
-                                                    schedule.get("order", 0))
-        cfg = ServerConfig(pool_bytes, max_batch, max_inflight, sc)
+        cfg = ServerConfig(pool_bytes, max_batch, max_inflight, Schedule.of(schedule))
         self._h = ctypes.c_void_p()
         _check(load().pg_server_create(ctypes.byref(cfg), ctypes.byref(self._h)))
 

@@ -389,6 +389,142 @@ __global__ void __launch_bounds__(S, PG12_MERKLE_MIN_BLOCKS * 256 / S) k_merkle(
     }
 }
 
+// ------------------------------------------- tensor-core batch kernel
+// Units of 128 nodes: level l of a tree of n leaves has
+// ceil((n >> l) / 128) of them.  A task is 2^fuse consecutive leaf units;
+// the group that takes it builds them and the fuse levels above them on its
+// own, then climbs with arrival counters: when the level below has at least
+// two units, the group that completes the second of two sibling units
+// builds their parent unit and goes on, the first goes back for a new task.
+// Levels of at most 128 nodes have one unit and are climbed directly.
+__device__ __forceinline__ uint64_t tc_units(uint64_t n, uint32_t l) {
+    return ((n >> l) + kTcGroup - 1) / kTcGroup;
+}
+
+// Unit u of level l of a tree: node k = 128 u + t of the level is the
+// sponge of leaf row k (l = 0) or the compression of children 2k, 2k + 1
+// (read from L2: other groups of this launch wrote them).  Rows past the
+// level's end are computed on zeros and not stored.
+__device__ __forceinline__ bool tc_unit(TcGroup &G, const TreePlan &tp, uint32_t l, uint64_t u) {
+    const uint64_t n = tp.n_leaves, cnt = n >> l;
+    const uint64_t k = u * kTcGroup + G.t;
+    const bool valid = k < cnt;
+    uint64_t *slot = G.slot + G.t;
+#pragma unroll
+    for (int i = kRate; i < kT; ++i) slot[i * kTcGroup] = 0;
+    if (l == 0) {
+        const uint64_t w = tp.width, chunks = (w + kRate - 1) / kRate;
+        const uint64_t *row = tp.rows + (valid ? k : 0) * w;
+        for (uint64_t c = 0; c < chunks; ++c) {
+            uint64_t ch[kRate];
+            load_chunk(row, w, c, tp.vec16 != 0, ch);
+#pragma unroll
+            for (int i = 0; i < kRate; ++i) slot[i * kTcGroup] = valid ? ch[i] : 0ull;
+            if (!tc_permute(G, c == 0, c + 1 == chunks)) return false;
+        }
+    } else {
+        const uint64_t *kids = tp.nodes + kDigest * (level_off(n, l - 1) + 2 * (valid ? k : 0));
+#pragma unroll
+        for (int i = 0; i < 2 * kDigest; i += 2) {
+            uint64_t a, b;
+            ld2_cg(kids + i, a, b);
+            slot[i * kTcGroup] = a;
+            slot[(i + 1) * kTcGroup] = b;
+        }
+        if (!tc_permute(G, true, true)) return false;
+    }
+    if (valid) {
+        uint64_t *dst = tp.nodes + kDigest * (level_off(n, l) + k);
+        st2(dst, canon(slot[0]), canon(slot[kTcGroup]));
+        st2(dst + 2, canon(slot[2 * kTcGroup]), canon(slot[3 * kTcGroup]));
+    }
+    return true;
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1) k_tc_batch(const TreePlan *__restrict__ plans, uint32_t n_trees,
+                                                            uint32_t total_tasks, uint32_t fuse,
+                                                            uint32_t *__restrict__ counters,
+                                                            uint32_t *__restrict__ next_task) {
+    extern __shared__ __align__(1024) uint8_t tc_sm[];
+    TcGroup G = tc_setup<kTcGroups>(tc_sm);
+    bool ok = true;
+    while (ok) {
+        const uint32_t task = group_fetch_add(G, next_task);
+        if (task >= total_tasks) break;
+        uint32_t lo_t = 0, hi_t = n_trees - 1;
+        while (lo_t < hi_t) {
+            const uint32_t mid = (lo_t + hi_t + 1) / 2;
+            if (plans[mid].leaf_task_begin <= task) lo_t = mid;
+            else hi_t = mid - 1;
+        }
+        const TreePlan &tp = plans[lo_t];
+        const uint64_t n = tp.n_leaves;
+        const uint32_t log_n = tp.log_n;
+        const uint32_t top = log_n < tp.climb_limit ? log_n : tp.climb_limit;
+        uint64_t lo = (uint64_t)(task - tp.leaf_task_begin) << fuse;
+        const uint64_t units0 = tc_units(n, 0);
+        uint64_t cnt = units0 - lo < (1ull << fuse) ? units0 - lo : (1ull << fuse);
+        for (uint32_t l = 0;; ++l) {
+            for (uint64_t i = 0; i < cnt && ok; ++i) ok = tc_unit(G, tp, l, lo + i);
+            if (!ok) break;
+            if (l == log_n) {
+                if (G.t == 0) signal_root(tp, 0);
+                break;
+            }
+            if (l == top) break;  // the levels above are built by k_batch_top
+            __threadfence();
+            if (cnt >= 2) {
+                // both children of every parent unit are this task's: no counter
+                group_sync(G.bar);
+                lo >>= 1;
+                cnt >>= 1;
+                continue;
+            }
+            if (tc_units(n, l) >= 2) {
+                const uint32_t old = group_fetch_add(G, &counters[tp.counter_base + tp.level_counter[l + 1] + (lo >> 1)]);
+                if (old == 0) break;  // the sibling unit is not done: its group builds the parent
+                __threadfence();
+            } else {
+                group_sync(G.bar);
+            }
+            lo >>= 1;
+        }
+    }
+    tc_teardown<kTcGroups>(tc_sm, G);
+}
+
+// The top levels of every tree of a batch whose persistent launch stopped
+// below them (climb_limit): one block per tree, 16 lanes per node (the
+// latency form), a block barrier between levels; at most 64 nodes a level.
+constexpr int kBatchTopThreads = 1024;
+constexpr uint64_t kBatchTopNodes = kBatchTopThreads / 16;
+__global__ void __launch_bounds__(kBatchTopThreads) k_batch_top(const TreePlan *__restrict__ plans) {
+    __shared__ __align__(16) DevConsts K;
+    load_consts(K);
+    const TreePlan &tp = plans[blockIdx.x];
+    const uint64_t n = tp.n_leaves;
+    const uint32_t log_n = tp.log_n;
+    if (tp.climb_limit >= log_n) return;  // this tree was climbed to its root
+    const uint64_t gid = threadIdx.x >> 4;
+    const int l16 = threadIdx.x & 15;
+    for (uint32_t level = tp.climb_limit + 1; level <= log_n; ++level) {
+        const uint64_t count = n >> level;
+        if ((gid & ~1ull) < count) {  // whole warps (groups 2w, 2w + 1)
+            const bool valid = gid < count;
+            const uint64_t node = valid ? gid : 0;
+            const uint64_t *kids = tp.nodes + kDigest * (level_off(n, level - 1) + 2 * node);
+            uint64_t x = 0;
+            if (l16 < 2 * kDigest) {
+                asm volatile("ld.global.cg.u64 %0, [%1];" : "=l"(x) : "l"(kids + l16));
+            }
+            x = permute_wide(x, l16, 0xFFFFFFFFu, K);
+            if (valid && l16 < kDigest) tp.nodes[kDigest * (level_off(n, level) + node) + l16] = canon(x);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) signal_root(tp, 0);
+}
+
 // ---------------------------------------------------- allocation-free build
 // For callers that cannot allocate device memory (for example code running
 // under an allocator that forbids cudaMalloc, or inside a host process that
@@ -665,7 +801,7 @@ const char *const kKernelNames[kIdCount] = {"k_merkle",      "k_merkle_top",    
                                             "k_ntt_pass",    "k_ntt_bitrev",    "k_merkle_level",
                                             "k_merkle_top_tail",
                                             "k_tc_permute",  "k_tc_sponge:leaves", "k_tc_sponge:level",
-                                            "k_tc_sponge:rows"};
+                                            "k_tc_sponge:rows", "k_tc_batch",  "k_batch_top"};
 constexpr size_t kProfMaxRecords = 1u << 16;
 
 struct ProfRecord {
@@ -737,10 +873,14 @@ uint32_t log2u(uint64_t x) {
     return l;
 }
 
-// Task geometry of one tree (see k_merkle).  n_counters receives the
-// number of arrival counters the tree needs; returns the leaf-task count.
+// Task geometry of one tree.  Integer engine (k_merkle): a task is 32
+// nodes of one level (unit_log 5, fuse 0).  Tensor engine (k_tc_batch): a
+// unit is 128 nodes (unit_log 7) and a leaf task 2^fuse leaf units.  Level
+// l >= 1 gets arrival counters (one per unit) when level l - 1 has at least
+// two units.  n_counters receives their number; returns the leaf tasks.
 uint32_t plan_tree(dev::TreePlan &tp, const uint64_t *rows, uint64_t n, uint64_t w, uint64_t *nodes,
-                   uint32_t leaf_task_begin, uint32_t counter_base, uint32_t &n_counters) {
+                   uint32_t leaf_task_begin, uint32_t counter_base, uint32_t &n_counters, uint32_t unit_log = 5,
+                   uint32_t fuse = 0) {
     tp.rows = rows;
     tp.nodes = nodes;
     tp.n_leaves = n;
@@ -752,15 +892,24 @@ uint32_t plan_tree(dev::TreePlan &tp, const uint64_t *rows, uint64_t n, uint64_t
     tp.climb_limit = tp.log_n;
     tp.done_flag = nullptr;
     n_counters = 0;
+    const uint64_t unit = 1ull << unit_log;
+    auto units = [&](uint32_t l) { return ((n >> l) + unit - 1) / unit; };
     for (uint32_t l = 0; l < (uint32_t)dev::kMaxLevels; ++l) tp.level_counter[l] = 0;
     for (uint32_t l = 1; l <= tp.log_n; ++l) {
-        const uint64_t below = n >> (l - 1);
-        if (below > (uint64_t)dev::kWarpNodes) {
+        if (units(l - 1) >= 2) {
             tp.level_counter[l] = n_counters;
-            n_counters += (uint32_t)(((n >> l) + dev::kWarpNodes - 1) / dev::kWarpNodes);
+            n_counters += (uint32_t)units(l);
         }
     }
-    return (uint32_t)((n + dev::kWarpNodes - 1) / dev::kWarpNodes);
+    return (uint32_t)((units(0) + (1ull << fuse) - 1) >> fuse);
+}
+
+// First level of a tree with at most 64 nodes (the top levels a 16-lane
+// launch builds when a schedule asks for top_lanes = 16).
+uint32_t first_small_level(uint64_t n) {
+    uint32_t l = 0;
+    while ((n >> l) > dev::kBatchTopNodes) ++l;
+    return l;
 }
 
 cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
@@ -770,14 +919,30 @@ pg_status require_init() {
     return PG_OK;
 }
 
+bool batch_uses_tc(const pg_schedule *sched) {
+    const uint32_t e = sched ? sched->engine : PG_BATCH_ENGINE_DEFAULT;
+    return e == PG_BATCH_ENGINE_TENSOR || (e == PG_BATCH_ENGINE_DEFAULT && g.engine == 1);
+}
+
 // Validate a batch and build its plans (in launch order).  Returns the
 // number of leaf tasks and counters through the out-parameters.
-pg_status plan_batch(const pg_tree *trees, size_t n_trees, const pg_schedule *sched,
-                     std::vector<dev::TreePlan> &plans, uint32_t &tasks, uint64_t &counters) {
+pg_status plan_batch(const pg_tree *trees, size_t n_trees, const pg_schedule *sched_in,
+                     std::vector<dev::TreePlan> &plans, uint32_t &tasks, uint64_t &counters, pg_schedule &resolved) {
+    // the schedule with its engine resolved once, so that plans and launch agree
+    std::memset(&resolved, 0, sizeof resolved);
+    if (sched_in) resolved = *sched_in;
+    if (resolved.engine == PG_BATCH_ENGINE_DEFAULT && resolved.reserved[0] == 0 && resolved.reserved[1] == 0)
+        resolved.engine = g.engine == 1 ? PG_BATCH_ENGINE_TENSOR : PG_BATCH_ENGINE_INT;
+    const pg_schedule *sched = &resolved;
     if (!trees || n_trees == 0) return fail(PG_ERR_INVALID_ARG, "empty batch");
-    if (sched && (sched->reserved != 0 || (sched->block != 0 && sched->block != 128 && sched->block != 256) ||
-                  sched->order > 1))
+    if (sched && (sched->reserved[0] != 0 || sched->reserved[1] != 0 ||
+                  (sched->block != 0 && sched->block != 128 && sched->block != 256) || sched->order > 1 ||
+                  sched->engine > PG_BATCH_ENGINE_TENSOR || sched->fuse_levels > 3 ||
+                  (sched->top_lanes != 0 && sched->top_lanes != 1 && sched->top_lanes != 16)))
         return fail(PG_ERR_INVALID_ARG, "bad schedule");
+    const bool tc = batch_uses_tc(sched);
+    const uint32_t unit_log = tc ? 7 : 5, fuse = tc && sched ? sched->fuse_levels : 0;
+    const bool handoff = sched && sched->top_lanes == 16;
     std::vector<size_t> idx(n_trees);
     for (size_t k = 0; k < n_trees; ++k) {
         const pg_tree &t = trees[k];
@@ -805,7 +970,11 @@ pg_status plan_batch(const pg_tree *trees, size_t n_trees, const pg_schedule *sc
         uint32_t nc = 0;
         std::memset(&plans[k], 0, sizeof(dev::TreePlan));
         const uint32_t tk = plan_tree(plans[k], t.rows, t.n_leaves, t.width, t.nodes, (uint32_t)task_sum,
-                                      (uint32_t)counter_sum, nc);
+                                      (uint32_t)counter_sum, nc, unit_log, fuse);
+        if (handoff) {
+            const uint32_t f = first_small_level(t.n_leaves);
+            plans[k].climb_limit = f == 0 ? 0 : f - 1;
+        }
         task_sum += tk;
         counter_sum += nc;
         if (task_sum >= (1ull << 32) || counter_sum >= (1ull << 32))
@@ -942,6 +1111,40 @@ pg_status launch_merkle(const pg_schedule *sched, const dev::TreePlan *d_plans, 
     return PG_OK;
 }
 
+// Permutations of the levels a top-level launch builds (climb_limit < log_n).
+uint64_t top_perms_of(const dev::TreePlan *plans, size_t n) {
+    uint64_t p = 0;
+    for (size_t k = 0; k < n; ++k)
+        if (plans[k].climb_limit < plans[k].log_n) p += (plans[k].n_leaves >> plans[k].climb_limit) - 1;
+    return p;
+}
+
+// The persistent kernel of a batch (tensor or integer engine), then, for
+// top_lanes = 16, the 16-lane launch of every tree's top levels.
+pg_status launch_batch(const pg_schedule *sched, const dev::TreePlan *d_plans, uint32_t n_trees, uint32_t tasks,
+                       uint32_t *d_counters, cudaStream_t st, uint64_t perms, uint64_t top_perms) {
+    if (batch_uses_tc(sched)) {
+        const uint32_t fuse = sched ? sched->fuse_levels : 0;
+        const uint32_t want = (tasks + dev::kTcGroups - 1) / dev::kTcGroups;
+        const unsigned grid = want < (uint32_t)g.sms ? want : (uint32_t)g.sms;
+        if (grid > 0) {
+            ProfScope prof(kIdTcBatch, st, perms - top_perms);
+            dev::k_tc_batch<<<grid, dev::kTcThreads, dev::TcL::kBytes, st>>>(d_plans, n_trees, tasks, fuse, d_counters + 1,
+                                                                              d_counters);
+            PG_CUDA(cudaGetLastError());
+        }
+    } else {
+        pg_status s = launch_merkle(sched, d_plans, n_trees, tasks, d_counters, st, perms - top_perms);
+        if (s != PG_OK) return s;
+    }
+    if (sched && sched->top_lanes == 16) {
+        ProfScope prof(kIdBatchTop, st, top_perms);
+        dev::k_batch_top<<<n_trees, dev::kBatchTopThreads, 0, st>>>(d_plans);
+        PG_CUDA(cudaGetLastError());
+    }
+    return PG_OK;
+}
+
 }  // namespace
 
 int ntt_require_init() {
@@ -994,7 +1197,7 @@ struct pg_batch_graph {
     size_t plan_bytes;
     uint32_t n_trees, tasks;
     uint64_t counters;
-    uint64_t perms;
+    uint64_t perms, top_perms;
     cudaGraph_t graph;
     cudaGraphExec_t exec;
     cudaStream_t capture;
@@ -1174,7 +1377,8 @@ bool server_step(pg_server *s) {
     std::vector<dev::TreePlan> plans;
     uint32_t tasks = 0;
     uint64_t counters = 0;
-    pg_status st = plan_batch(trees.data(), trees.size(), &s->cfg.sched, plans, tasks, counters);
+    pg_schedule rs;
+    pg_status st = plan_batch(trees.data(), trees.size(), &s->cfg.sched, plans, tasks, counters, rs);
     cudaError_t e = cudaSuccess;
     if (st == PG_OK) {
         // plans may be reordered: match each plan to its request by node buffer
@@ -1191,8 +1395,9 @@ bool server_step(pg_server *s) {
         if (e == cudaSuccess)
             e = cudaMemsetAsync(slot->d_counters, 0, sizeof(uint32_t) * (1 + (size_t)counters), slot->stream);
         if (e == cudaSuccess)
-            st = launch_merkle(&s->cfg.sched, slot->d_plans, (uint32_t)plans.size(), tasks, slot->d_counters,
-                               slot->stream, batch_perms(trees.data(), trees.size()));
+            st = launch_batch(&rs, slot->d_plans, (uint32_t)plans.size(), tasks, slot->d_counters,
+                              slot->stream, batch_perms(trees.data(), trees.size()),
+                              top_perms_of(plans.data(), plans.size()));
         if (e == cudaSuccess && st == PG_OK) e = cudaEventRecord(slot->done, slot->stream);
     }
     const double t = s->now();
@@ -1364,6 +1569,7 @@ pg_status pg_init(int device, const char *params_path) {
     if (s != PG_OK) return s;
     PG_CUDA(cudaFuncSetAttribute(dev::k_tc_permute, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dev::TcL::kBytes));
     PG_CUDA(cudaFuncSetAttribute(dev::k_tc_sponge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dev::TcL::kBytes));
+    PG_CUDA(cudaFuncSetAttribute(dev::k_tc_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dev::TcL::kBytes));
     {
         const int ns = ntt_upload_constants();
         if (ns != PG_OK) return (pg_status)ns;
@@ -1575,7 +1781,8 @@ pg_status pg_merkle_build_batch(const pg_tree *trees, size_t n_trees, const pg_s
     std::vector<dev::TreePlan> plans;
     uint32_t tasks = 0;
     uint64_t counters = 0;
-    s = plan_batch(trees, n_trees, sched, plans, tasks, counters);
+    pg_schedule rs;
+    s = plan_batch(trees, n_trees, sched, plans, tasks, counters, rs);
     if (s != PG_OK) return s;
     const size_t plan_bytes = plans.size() * sizeof(dev::TreePlan);
     const size_t counter_bytes = sizeof(uint32_t) * (1 + (size_t)counters);
@@ -1587,7 +1794,8 @@ pg_status pg_merkle_build_batch(const pg_tree *trees, size_t n_trees, const pg_s
     auto *d_counters = reinterpret_cast<uint32_t *>(g.ws + kPlanBytes);
     PG_CUDA(cudaMemcpyAsync(d_plan, plans.data(), plan_bytes, cudaMemcpyHostToDevice, st));
     PG_CUDA(cudaMemsetAsync(d_counters, 0, counter_bytes, st));
-    return launch_merkle(sched, d_plan, (uint32_t)plans.size(), tasks, d_counters, st, batch_perms(trees, n_trees));
+    return launch_batch(&rs, d_plan, (uint32_t)plans.size(), tasks, d_counters, st, batch_perms(trees, n_trees),
+                        top_perms_of(plans.data(), plans.size()));
 }
 
 pg_status pg_batch_graph_create(const pg_tree *trees, size_t n_trees, const pg_schedule *sched,
@@ -1599,18 +1807,19 @@ pg_status pg_batch_graph_create(const pg_tree *trees, size_t n_trees, const pg_s
     std::vector<dev::TreePlan> plans;
     uint32_t tasks = 0;
     uint64_t counters = 0;
-    s = plan_batch(trees, n_trees, sched, plans, tasks, counters);
+    pg_schedule rs;
+    s = plan_batch(trees, n_trees, sched, plans, tasks, counters, rs);
     if (s != PG_OK) return s;
     auto *h = new (std::nothrow) pg_batch_graph();
     if (!h) return fail(PG_ERR_OOM, "host allocation failed");
     h->device = g.device;
-    std::memset(&h->sched, 0, sizeof h->sched);
-    if (sched) h->sched = *sched;
+    h->sched = rs;
     h->plan_bytes = plans.size() * sizeof(dev::TreePlan);
     h->n_trees = (uint32_t)plans.size();
     h->tasks = tasks;
     h->counters = counters;
     h->perms = batch_perms(trees, n_trees);
+    h->top_perms = top_perms_of(plans.data(), plans.size());
     const size_t plan_bytes_aligned = (h->plan_bytes + 255) & ~(size_t)255;
     const size_t total = plan_bytes_aligned + sizeof(uint32_t) * (1 + (size_t)counters);
     cudaError_t e = cudaMalloc(&h->dmem, total);
@@ -1635,7 +1844,7 @@ pg_status pg_batch_graph_create(const pg_tree *trees, size_t n_trees, const pg_s
     e = cudaStreamBeginCapture(h->capture, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cleanup(fail(PG_ERR_CUDA, "begin capture: %s", cudaGetErrorString(e)));
     cudaError_t e_memset = cudaMemsetAsync(d_counters, 0, sizeof(uint32_t) * (1 + (size_t)counters), h->capture);
-    pg_status sl = launch_merkle(&h->sched, d_plan, h->n_trees, tasks, d_counters, h->capture, h->perms);
+    pg_status sl = launch_batch(&h->sched, d_plan, h->n_trees, tasks, d_counters, h->capture, h->perms, h->top_perms);
     e = cudaStreamEndCapture(h->capture, &h->graph);
     if (e_memset != cudaSuccess || sl != PG_OK || e != cudaSuccess)
         return cleanup(sl != PG_OK ? sl : fail(PG_ERR_CUDA, "capture: %s", cudaGetErrorString(e != cudaSuccess ? e : e_memset)));
@@ -1670,46 +1879,57 @@ pg_status pg_batch_autotune(const pg_tree *trees, size_t n_trees, void *stream, 
     if (s != PG_OK) return s;
     if (!best) return fail(PG_ERR_INVALID_ARG, "best is NULL");
     cudaStream_t st = as_stream(stream);
+    std::vector<pg_schedule> cands;
+    for (uint32_t order = 0; order <= 1; ++order)
+        for (uint32_t top : {1u, 16u}) {
+            for (uint32_t fuse = 0; fuse <= 2; ++fuse) {
+                pg_schedule c{};
+                c.engine = PG_BATCH_ENGINE_TENSOR;
+                c.order = order;
+                c.fuse_levels = fuse;
+                c.top_lanes = top;
+                cands.push_back(c);
+            }
+            for (uint32_t b : {256u, 128u}) {
+                pg_schedule c{};
+                c.engine = PG_BATCH_ENGINE_INT;
+                c.block = b;
+                c.order = order;
+                c.top_lanes = top;
+                cands.push_back(c);
+            }
+        }
     cudaEvent_t e0, e1;
     PG_CUDA(cudaEventCreate(&e0));
     PG_CUDA(cudaEventCreate(&e1));
-    float top = -1.f;
+    float top_ms = -1.f;
     pg_schedule win{};
-    const uint32_t blocks[2] = {256, 128};
-    for (uint32_t b : blocks) {
-        const int occ = b == 128 ? g.merkle128_blocks_per_sm : g.merkle_blocks_per_sm;
-        for (int bps = occ; bps >= 1 && bps >= occ - 1; --bps) {
-            for (uint32_t order = 0; order <= 1; ++order) {
-                pg_schedule c{b, (uint32_t)bps, order, 0};
-                s = pg_merkle_build_batch(trees, n_trees, &c, stream);  // warm-up
-                if (s != PG_OK) break;
-                float tot = 0.f;
-                const int reps = 3;
-                for (int r = 0; r < reps && s == PG_OK; ++r) {
-                    cudaEventRecord(e0, st);
-                    s = pg_merkle_build_batch(trees, n_trees, &c, stream);
-                    cudaEventRecord(e1, st);
-                    cudaEventSynchronize(e1);
-                    float ms = 0.f;
-                    cudaEventElapsedTime(&ms, e0, e1);
-                    tot += ms;
-                }
-                if (s != PG_OK) break;
-                const float avg = tot / reps;
-                if (top < 0.f || avg < top) {
-                    top = avg;
-                    win = c;
-                }
-            }
-            if (s != PG_OK) break;
+    for (const pg_schedule &c : cands) {
+        s = pg_merkle_build_batch(trees, n_trees, &c, stream);  // warm-up
+        if (s != PG_OK) break;
+        float tot = 0.f;
+        const int reps = 3;
+        for (int r = 0; r < reps && s == PG_OK; ++r) {
+            cudaEventRecord(e0, st);
+            s = pg_merkle_build_batch(trees, n_trees, &c, stream);
+            cudaEventRecord(e1, st);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            tot += ms;
         }
         if (s != PG_OK) break;
+        const float avg = tot / reps;
+        if (top_ms < 0.f || avg < top_ms) {
+            top_ms = avg;
+            win = c;
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (s != PG_OK) return s;
     *best = win;
-    if (best_ms) *best_ms = top;
+    if (best_ms) *best_ms = top_ms;
     return PG_OK;
 }
 

@@ -73,7 +73,7 @@ int set_error(int status, const char *fmt, ...);
 enum KernelId {
     kIdMerkle, kIdMerkleTop, kIdMerkleTopLeaf, kIdPermute, kIdHashRows, kIdOpen, kIdVerify, kIdSingle,
     kIdGraph, kIdNttPass, kIdNttBitrev, kIdMerkleLevel, kIdMerkleTopTail,
-    kIdTcPermute, kIdTcLeaves, kIdTcLevel, kIdTcRows, kIdCount
+    kIdTcPermute, kIdTcLeaves, kIdTcLevel, kIdTcRows, kIdTcBatch, kIdBatchTop, kIdCount
 };
 
 class ProfScope {

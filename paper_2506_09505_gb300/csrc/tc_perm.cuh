@@ -63,6 +63,8 @@ __device__ __forceinline__ void tc_commit(uint64_t *mbar) {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void group_sync(int id) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(kTcGroup) : "memory"); }
+
 // Barrier of a group's 128 threads that also ORs a flag over them (the
 // same answer in every thread).
 __device__ __forceinline__ uint32_t group_sync_or(int id, uint32_t flag) {
@@ -130,6 +132,7 @@ struct TcGroup {
     int bar;              // named barrier of the group's 128 threads
     int t;                // thread index within the group
     uint32_t failed;      // this thread saw a tensor-core wait run out
+    volatile uint32_t *bcast;  // one word through which thread 0 hands the group a value
     uint32_t a_addr, b_addr, bias_addr, zcap_addr;  // shared addresses for the descriptors
 };
 
@@ -212,7 +215,8 @@ struct TcLayout {
     static constexpr size_t kA = (sizeof(TcTables) + 127) & ~(size_t)127;
     static constexpr size_t kSlot = kA + (size_t)GROUPS * kTcABytes;
     static constexpr size_t kBar = kSlot + (size_t)GROUPS * kTcSlotBytes;
-    static constexpr size_t kBytes = kBar + 8 * GROUPS + 16;
+    static constexpr size_t kBcast = kBar + 8 * GROUPS + 16;
+    static constexpr size_t kBytes = kBcast + 4 * GROUPS;
 };
 
 __device__ int g_tc_fault;  // set when a tensor-core wait ran out (read by pg_device_flags)
@@ -250,12 +254,24 @@ __device__ __forceinline__ TcGroup tc_setup(uint8_t *sm) {
     G.tmem = *tslot + (uint32_t)(g * kTcTmemCols);
     G.phase = 0;
     G.bar = 1 + g;
+    G.bcast = reinterpret_cast<volatile uint32_t *>(sm + L::kBcast) + g;
     const TcTables *T = reinterpret_cast<const TcTables *>(sm + L::kTables);
     G.a_addr = smem_addr(G.a);
     G.b_addr = smem_addr(T->b[0]);
     G.bias_addr = smem_addr(T->a_bias);
     G.zcap_addr = smem_addr(T->a_zcap);
     return G;
+}
+
+// Thread 0 adds one to *counter; every thread of the group gets the old
+// value.  The first barrier orders the group's earlier stores (each thread
+// fences its own first) before the atomic and keeps thread 0 from
+// overwriting a value others have not read yet.
+__device__ __forceinline__ uint32_t group_fetch_add(TcGroup &G, uint32_t *counter) {
+    group_sync(G.bar);
+    if (G.t == 0) *G.bcast = atomicAdd(counter, 1u);
+    group_sync(G.bar);
+    return *G.bcast;
 }
 
 // Epilogue: every group is done with tensor memory; the allocating warp

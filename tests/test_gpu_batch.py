@@ -37,8 +37,17 @@ def _mix(seed=0x900):
     return host_rows, [_dev(r) for r in host_rows]
 
 
-@pytest.mark.parametrize("sched", [None, {"block": 128}, {"block": 256, "order": 1},
-                                   {"block": 128, "blocks_per_sm": 1, "order": 1}])
+INT, TC = pg.BATCH_ENGINE_INT, pg.BATCH_ENGINE_TENSOR
+SCHEDULES = [None,
+             {"engine": INT, "block": 128}, {"engine": INT, "block": 256, "order": 1},
+             {"engine": INT, "block": 128, "blocks_per_sm": 1, "order": 1},
+             {"engine": INT, "top_lanes": 16},
+             {"engine": TC}, {"engine": TC, "order": 1}, {"engine": TC, "fuse_levels": 1},
+             {"engine": TC, "fuse_levels": 2, "top_lanes": 16}, {"engine": TC, "fuse_levels": 3, "order": 1},
+             {"engine": TC, "top_lanes": 16}]
+
+
+@pytest.mark.parametrize("sched", SCHEDULES)
 def test_batch_equals_oracle(sched):
     host_rows, rows = _mix()
     nodes = pg.merkle_build_batch(rows, schedule=sched)
@@ -46,12 +55,22 @@ def test_batch_equals_oracle(sched):
         assert (_host(nd) == oracle.merkle_build(hr, nthreads=8)).all()
 
 
-def test_batch_equals_single_builds_larger_trees():
+@pytest.mark.parametrize("sched", [{"order": 1}, {"engine": TC, "fuse_levels": 2, "order": 1},
+                                   {"engine": TC, "fuse_levels": 1, "top_lanes": 16}])
+def test_batch_equals_single_builds_larger_trees(sched):
     sizes = [(14, 8), (16, 8), (13, 64), (15, 16), (12, 128), (16, 32)]
     rows = [_dev(pg_synth.matrix(0xA00 + k, 1 << lg, w)) for k, (lg, w) in enumerate(sizes)]
-    batch = pg.merkle_build_batch(rows, schedule={"order": 1})
+    batch = pg.merkle_build_batch(rows, schedule=sched)
     for r, nd in zip(rows, batch):
         assert torch.equal(nd, pg.merkle_build(r))
+
+
+def test_batch_rejects_bad_schedules():
+    _, rows = _mix(0xE00)
+    for bad in ({"engine": 3}, {"fuse_levels": 4}, {"top_lanes": 8}, {"block": 64}, {"order": 2}):
+        with pytest.raises(pg.PGError) as e:
+            pg.merkle_build_batch(rows, schedule=bad)
+        assert e.value.status == 1, bad
 
 
 def test_batch_graph_replays_identically():
@@ -89,7 +108,11 @@ def test_batch_graph_on_side_stream():
 def test_autotune_returns_a_valid_schedule():
     _, rows = _mix(0xC00)
     best, ms = pg.batch_autotune(rows)
-    assert best["block"] in (128, 256) and best["order"] in (0, 1) and best["blocks_per_sm"] >= 1
+    assert best["engine"] in (INT, TC) and best["order"] in (0, 1) and best["top_lanes"] in (1, 16)
+    if best["engine"] == INT:
+        assert best["block"] in (128, 256)
+    else:
+        assert best["fuse_levels"] in (0, 1, 2)
     assert ms > 0
     nodes = pg.merkle_build_batch(rows, schedule=best)
     for r, nd in zip(rows, nodes):

@@ -93,7 +93,7 @@ def test_other_entry_points_are_recorded():
     assert got["k_tc_sponge:rows"]["perms"] == 1024
     batch = _tree_perms(1 << 9, 8) + _tree_perms(1 << 11, 16)
     # the batch launch and the graph launch (captured launches are not recorded)
-    assert got["k_merkle"]["launches"] == 1 and got["k_merkle"]["perms"] == batch
+    assert got["k_tc_batch"]["launches"] == 1 and got["k_tc_batch"]["perms"] == batch
     assert got["batch_graph"]["launches"] == 1 and got["batch_graph"]["perms"] == batch
 
 
