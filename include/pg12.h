@@ -292,14 +292,16 @@ pg_status pg_hash_rows(const uint64_t *rows, size_t n_rows, size_t width, uint64
  *             of nodes 2k and 2k+1 of level l-1.
  *   root_out  host, 4 words, or NULL.  When non-NULL the call synchronises
  *             `stream` and copies the root there.
- * Launches: the leaf sponges in the persistent kernel (trees of at most
- * 8,192 leaves: in the 16-lanes-per-state form), then one launch per level
- * of more than 64 nodes and one launch of an 8-block cluster for all levels
- * of at most 64 nodes up to the root.  Level launches use programmatic
+ * Launches: the leaf sponges in one launch (the tensor-core kernel, or the
+ * integer-pipe kernel under PG_ENGINE_INT; trees of at most 8,192 leaves:
+ * the 16-lanes-per-state form), then one launch per level of more than 64
+ * nodes and one launch of an 8-block cluster for all levels of at most 64
+ * nodes up to the root.  Level launches use programmatic
  * dependent launch: each may be scheduled while the previous one finishes,
  * and reads its input only once that one has completed.
- * Uses the library workspace (allocated in pg_init) for its task counter;
- * concurrent builds on different streams are not supported.
+ * Reads and writes nothing but rows and nodes (no library workspace), so
+ * builds of different trees on different streams may run concurrently.
+ * rows and nodes must not overlap (PG_ERR_INVALID_ARG).
  */
 pg_status pg_merkle_build(const uint64_t *rows, size_t n_leaves, size_t width, uint64_t *nodes,
                           uint64_t *root_out, void *stream);
@@ -453,12 +455,16 @@ pg_status pg_merkle_verify(const uint64_t *root, size_t n_leaves, const uint64_t
  *   stream                        cudaStream_t as void* (NULL = default).
  * Allocates nothing and does not need pg_init().  Its scratch (the arrival
  * counters of the build, 512 KiB) is a file-scope __device__ array that every
- * GPU loading the library holds until process exit.  The first call on a
- * device performs that device's set-up (uploads the constant tables and
- * looks up the array's device address) with the device current; make that
- * first call before any stream capture.  All calls share the one array,
- * which keeps the previous call's contents (each call clears what it uses):
- * calls that overlap on the GPU race and must be serialised by the caller.
+ * GPU loading the library holds until process exit, one copy per device.
+ * The first call on a device, and the first call on it after the active
+ * parameter set changed (pg_params_select, pg_init with another set),
+ * performs that device's set-up (a synchronous upload of the constant
+ * tables, and the lookup of the array's device address) with the device
+ * current; make those calls before any stream capture.  All calls on one
+ * device share that device's array, which keeps the previous call's contents
+ * (each call clears what it uses): calls that overlap on the same GPU race
+ * and must be serialised by the caller.  rows and nodes must not overlap
+ * (PG_ERR_INVALID_ARG).
  * Asynchronous on `stream`; no root is returned (read it from nodes).
  */
 pg_status pg_merkle_build_noalloc(const uint64_t *rows, size_t n_leaves, size_t width, uint64_t *nodes,

@@ -197,13 +197,16 @@ __global__ void __launch_bounds__(kSmallBlock) k_merkle_level(const uint64_t *__
 
 // ------------------------------------------------- tensor-core kernels
 // Persistent kernels of kTcGroups groups of 128 threads (one CTA per SM:
-// its tables, operands and slots take ~187 KiB of shared memory and its
-// groups all 512 columns of tensor memory).  Group q of CTA c takes units
+// with four groups its tables, operands and slots take 187 KB of shared
+// memory and its groups 384 of the 512 columns of tensor memory).  Group q of CTA c takes units
 // c * kTcGroups + q, then every gridDim.x * kTcGroups-th after: a static
 // schedule with no shared counter, so launches on different streams are
 // independent.  A unit is 128 consecutive states or rows; rows past the end
 // are computed on zeros and not stored.
-constexpr int kTcGroups = 4;
+#ifndef PG12_TC_GROUPS
+#define PG12_TC_GROUPS 4  // groups per CTA: 4 (16 warps) or 5 (20 warps, 223 KB of shared memory; measured 1.3% slower)
+#endif
+constexpr int kTcGroups = PG12_TC_GROUPS;
 constexpr int kTcThreads = kTcGroup * kTcGroups;
 using TcL = TcLayout<kTcGroups>;
 
@@ -332,6 +335,23 @@ __device__ __forceinline__ void signal_root(const TreePlan &tp, int lane) {
         __threadfence_system();
         *reinterpret_cast<volatile uint32_t *>(tp.done_flag) = 1u;
     }
+}
+
+// Leaf sponges of one tree on the integer pipes, one 32-leaf task per warp
+// in a static schedule (warp w of the grid takes tasks w, w + W, ...; tasks
+// are uniform, so no counter is needed), the plan passed by value: the
+// launch reads and writes nothing but the rows and the leaf digests, so
+// builds on different streams do not share any state.
+template <int MDS>
+__global__ void __launch_bounds__(kBlock, PG12_MERKLE_MIN_BLOCKS) k_merkle_leaves(const TreePlan tp,
+                                                                                uint32_t total_tasks) {
+    __shared__ uint64_t slots[kT * kBlock];
+    uint64_t *slot = slots + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    pdl_trigger();
+    const uint32_t warps = gridDim.x * (kBlock / 32);
+    for (uint32_t task = blockIdx.x * (kBlock / 32) + threadIdx.x / 32; task < total_tasks; task += warps)
+        run_warp_task<kBlock, MDS, true>(tp, 0, task, lane, slot);
 }
 
 // Persistent Merkle kernel: every warp pulls leaf tasks from a global
@@ -729,6 +749,7 @@ struct Context {
     int device = -1;
     int sms = 0;
     int merkle_blocks_per_sm = 0;      // k_merkle<256, *> (both matrix kinds: minimum)
+    int leaves_blocks_per_sm = 0;      // k_merkle_leaves<*>
     int merkle128_blocks_per_sm = 0;   // k_merkle<128, *>
     int permute_blocks_per_sm = 0;
     uint8_t *ws = nullptr;  // device workspace
@@ -773,16 +794,13 @@ namespace {
 constexpr size_t kWorkspaceBytes = 32u << 20;  // tree plans + arrival counters
 // pg_merkle_build's split of a tree between kernels.  Trees of at most
 // kSmallTree leaves run entirely in the 16-lanes-per-state kernels.  In
-// larger trees the persistent kernel builds the levels with more than
-// kTopNodes nodes (by default only the leaves: one launch per level measured
-// faster than climbing with arrival counters, 16.7 against 17.4 ms for a
-// 2^22 x 8 tree), and every other level is one launch: one thread per node
-// (k_merkle_level) while the level has more than kWideNodes nodes, the
-// 16-lanes-per-state kernel above that.
-#ifndef PG12_TOP_NODES
-#define PG12_TOP_NODES (1ull << 40)
-#endif
-constexpr uint64_t kTopNodes = PG12_TOP_NODES;
+// larger trees one launch hashes the leaves and every level is one launch
+// (one launch per level measured faster than climbing with arrival counters
+// in one persistent launch: 16.7 against 17.4 ms for a 2^22 x 8 tree on the
+// integer pipes, 10.20 against 10.73 ms with the tensor-core kernel): the
+// tensor-core kernel for levels of at least tc_min_nodes nodes, one thread
+// per node (k_merkle_level) while the level has more than kWideNodes nodes,
+// the 16-lanes-per-state kernel above that.
 #ifndef PG12_WIDE_NODES
 #define PG12_WIDE_NODES 8192
 #endif
@@ -867,6 +885,12 @@ pg_status upload_tables() {
 }
 
 bool is_pow2(uint64_t x) { return x && !(x & (x - 1)); }
+
+// Do the byte ranges [a, a + na) and [b, b + nb) share an address?
+bool overlaps(const void *a, size_t na, const void *b, size_t nb) {
+    const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+    return na && nb && x < y + nb && y < x + na;
+}
 uint32_t log2u(uint64_t x) {
     uint32_t l = 0;
     while ((1ull << l) < x) ++l;
@@ -954,7 +978,22 @@ pg_status plan_batch(const pg_tree *trees, size_t n_trees, const pg_schedule *sc
         if (reinterpret_cast<uintptr_t>(t.rows) % 8) return fail(PG_ERR_INVALID_ARG, "tree %zu: rows not 8-byte aligned", k);
         if (reinterpret_cast<uintptr_t>(t.nodes) % 16)
             return fail(PG_ERR_INVALID_ARG, "tree %zu: nodes not 16-byte aligned", k);
+        if (overlaps(t.rows, (size_t)t.n_leaves * t.width * 8, t.nodes, ((size_t)2 * t.n_leaves - 1) * 32))
+            return fail(PG_ERR_INVALID_ARG, "tree %zu: rows and nodes overlap", k);
         idx[k] = k;
+    }
+    // node buffers are written concurrently: no two may share an address
+    {
+        std::vector<std::pair<uintptr_t, size_t>> spans(n_trees);
+        for (size_t k = 0; k < n_trees; ++k)
+            spans[k] = {reinterpret_cast<uintptr_t>(trees[k].nodes), k};
+        std::sort(spans.begin(), spans.end());
+        for (size_t k = 1; k < n_trees; ++k) {
+            const pg_tree &a = trees[spans[k - 1].second];
+            if (spans[k - 1].first + ((size_t)2 * a.n_leaves - 1) * 32 > spans[k].first)
+                return fail(PG_ERR_INVALID_ARG, "trees %zu and %zu: node buffers overlap", spans[k - 1].second,
+                            spans[k].second);
+        }
     }
     if (sched && sched->order == 1) {
         auto work = [&](size_t k) {
@@ -1587,11 +1626,16 @@ pg_status pg_init(int device, const char *params_path) {
         PG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d, dev::k_merkle<128, dev::kMdsSmall>, 128, 0));
         PG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&e, dev::k_permute<dev::kMdsFull>, dev::kSmallBlock, 0));
         PG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&f, dev::k_permute<dev::kMdsSmall>, dev::kSmallBlock, 0));
+        int la = 0, lb = 0;
+        PG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&la, dev::k_merkle_leaves<dev::kMdsFull>, dev::kBlock, 0));
+        PG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&lb, dev::k_merkle_leaves<dev::kMdsSmall>, dev::kBlock, 0));
+        g.leaves_blocks_per_sm = la < lb ? la : lb;
         g.merkle_blocks_per_sm = a < b ? a : b;
         g.merkle128_blocks_per_sm = c < d ? c : d;
         g.permute_blocks_per_sm = e < f ? e : f;
     }
-    if (g.merkle_blocks_per_sm < 1 || g.merkle128_blocks_per_sm < 1 || g.permute_blocks_per_sm < 1)
+    if (g.merkle_blocks_per_sm < 1 || g.merkle128_blocks_per_sm < 1 || g.permute_blocks_per_sm < 1 ||
+        g.leaves_blocks_per_sm < 1)
         return fail(PG_ERR_CUDA, "kernels cannot be resident (occupancy 0)");
     void *ws = nullptr;
     cudaError_t e = cudaMalloc(&ws, kWorkspaceBytes);
@@ -1677,46 +1721,34 @@ pg_status pg_merkle_build(const uint64_t *rows, size_t n_leaves, size_t width, u
     if (n_leaves > (1ull << 34)) return fail(PG_ERR_INVALID_ARG, "n_leaves=%zu above 2^34", n_leaves);
     if (reinterpret_cast<uintptr_t>(rows) % 8) return fail(PG_ERR_INVALID_ARG, "rows not 8-byte aligned");
     if (reinterpret_cast<uintptr_t>(nodes) % 16) return fail(PG_ERR_INVALID_ARG, "nodes not 16-byte aligned");
-    dev::TreePlan tp;
-    std::memset(&tp, 0, sizeof tp);
-    uint32_t n_counters = 0;
-    const uint32_t tasks = plan_tree(tp, rows, n_leaves, width, nodes, 0, 0, n_counters);
-    // levels with at most kTopNodes nodes are built one launch per level,
-    // after the persistent kernel
-    uint32_t first_top = tp.log_n + 1;
-    for (uint32_t l = 1; l <= tp.log_n; ++l)
-        if ((n_leaves >> l) <= (uint64_t)kTopNodes) {
-            first_top = l;
-            break;
-        }
-    tp.climb_limit = first_top - 1;
-    const size_t counter_bytes = sizeof(uint32_t) * (1 + (size_t)n_counters);
-    if (sizeof(tp) > kPlanBytes || counter_bytes > g.ws_bytes - kPlanBytes)
-        return fail(PG_ERR_OOM, "workspace too small for %zu leaves", n_leaves);
+    if (overlaps(rows, (size_t)n_leaves * width * 8, nodes, ((size_t)2 * n_leaves - 1) * 32))
+        return fail(PG_ERR_INVALID_ARG, "rows and nodes overlap");
     cudaStream_t st = as_stream(stream);
-    const bool small = (uint64_t)n_leaves <= kSmallTree;  // whole tree in the wide form
-    if (small) first_top = 1;
-    auto *d_plan = reinterpret_cast<dev::TreePlan *>(g.ws);
-    auto *d_counters = reinterpret_cast<uint32_t *>(g.ws + kPlanBytes);
-    if (small) {
+    // the leaves in one launch, then one launch per level (launch_levels);
+    // nothing but rows and nodes is read or written, so concurrent builds on
+    // different streams are independent
+    const uint32_t first_top = 1;
+    if ((uint64_t)n_leaves <= kSmallTree) {  // whole tree in the 16-lane form
         const uint64_t threads = (uint64_t)n_leaves * 16;
         const unsigned grid = (unsigned)((threads + dev::kTopBlock - 1) / dev::kTopBlock);
         ProfScope prof(kIdMerkleTopLeaf, st, (uint64_t)n_leaves * ((width + kRate - 1) / kRate));
         dev::k_merkle_top_leaf<<<grid, dev::kTopBlock, 0, st>>>(rows, (uint64_t)n_leaves, (uint64_t)width, nodes);
         PG_CUDA(cudaGetLastError());
     } else if (g.engine == 1) {
-        // leaf sponges on the tensor-core kernel (no plan, no counters)
-        first_top = 1;
         s = launch_tc_sponge(rows, n_leaves, width, nodes, st, false, kIdTcLeaves);
         if (s != PG_OK) return s;
     } else {
-        PG_CUDA(cudaMemcpyAsync(d_plan, &tp, sizeof tp, cudaMemcpyHostToDevice, st));
-        // the task counter, plus the arrival counters when the kernel climbs
-        PG_CUDA(cudaMemsetAsync(d_counters, 0, tp.climb_limit ? counter_bytes : sizeof(uint32_t), st));
-        // leaf sponges plus the nodes of levels 1 .. first_top-1
-        const uint64_t perms = tree_perms(n_leaves, width) - ((n_leaves >> (first_top - 1)) - 1);
-        s = launch_merkle(nullptr, d_plan, 1u, tasks, d_counters, st, perms, true);
-        if (s != PG_OK) return s;
+        dev::TreePlan tp;
+        std::memset(&tp, 0, sizeof tp);
+        uint32_t n_counters = 0;
+        const uint32_t tasks = plan_tree(tp, rows, n_leaves, width, nodes, 0, 0, n_counters);
+        const uint32_t want = (tasks + dev::kBlock / 32 - 1) / (dev::kBlock / 32);
+        const uint32_t cap = (uint32_t)(g.sms * g.leaves_blocks_per_sm);
+        const unsigned grid = want < cap ? want : cap;
+        ProfScope prof(kIdMerkle, st, (uint64_t)n_leaves * ((width + kRate - 1) / kRate));
+        if (g.params_set == 1) dev::k_merkle_leaves<dev::kMdsSmall><<<grid, dev::kBlock, 0, st>>>(tp, tasks);
+        else dev::k_merkle_leaves<dev::kMdsFull><<<grid, dev::kBlock, 0, st>>>(tp, tasks);
+        PG_CUDA(cudaGetLastError());
     }
     s = launch_levels(nodes, n_leaves, first_top, st);
     if (s != PG_OK) return s;
@@ -1737,6 +1769,8 @@ pg_status pg_merkle_build_host(const uint64_t *rows_host, size_t n_leaves, size_
     if (n_leaves > (1ull << 34)) return fail(PG_ERR_INVALID_ARG, "n_leaves=%zu above 2^34", n_leaves);
     if (reinterpret_cast<uintptr_t>(rows_dev) % 8) return fail(PG_ERR_INVALID_ARG, "rows_dev not 8-byte aligned");
     if (reinterpret_cast<uintptr_t>(nodes) % 16) return fail(PG_ERR_INVALID_ARG, "nodes not 16-byte aligned");
+    if (overlaps(rows_dev, (size_t)n_leaves * width * 8, nodes, ((size_t)2 * n_leaves - 1) * 32))
+        return fail(PG_ERR_INVALID_ARG, "rows_dev and nodes overlap");
     cudaStream_t st = as_stream(stream);
     const uint64_t n = n_leaves, bytes_per_row = 8 * (uint64_t)width;
     // below 64 MiB of rows the copy takes less than the extra launches would
@@ -2110,11 +2144,13 @@ pg_status pg_merkle_verify(const uint64_t *root, size_t n_leaves, const uint64_t
 }
 
 // Allocation-free variant of pg_merkle_build (declared in include/pg12.h).
-// Its first call on a device does that device's set-up, with the device
-// current: it uploads the constant tables (cudaMemcpyToSymbol) and resolves
-// the device address of g_noalloc_scratch once with cudaGetSymbolAddress --
-// in host code the array's name is only a host-side stand-in and must never
-// be handed to a kernel.  Make that first call before any stream capture.
+// Its first call on a device, and its first call on that device after the
+// active parameter set has changed, does the set-up with the device current:
+// it uploads the constant tables (cudaMemcpyToSymbol, synchronous) and
+// resolves the device address of g_noalloc_scratch with
+// cudaGetSymbolAddress -- in host code the array's name is only a host-side
+// stand-in and must never be handed to a kernel.  Make those calls before
+// any stream capture.
 pg_status pg_merkle_build_noalloc(const uint64_t *rows, size_t n_leaves, size_t width, uint64_t *nodes,
                                   void *stream) {
     constexpr int kMaxDevices = 64;
@@ -2130,11 +2166,15 @@ pg_status pg_merkle_build_noalloc(const uint64_t *rows, size_t n_leaves, size_t 
                     (unsigned long long)dev::kNoAllocMaxLeaves);
     if (reinterpret_cast<uintptr_t>(rows) % 8) return fail(PG_ERR_INVALID_ARG, "rows not 8-byte aligned");
     if (reinterpret_cast<uintptr_t>(nodes) % 16) return fail(PG_ERR_INVALID_ARG, "nodes not 16-byte aligned");
+    if (overlaps(rows, (size_t)n_leaves * width * 8, nodes, ((size_t)2 * n_leaves - 1) * 32))
+        return fail(PG_ERR_INVALID_ARG, "rows and nodes overlap");
     int device = 0;
     PG_CUDA(cudaGetDevice(&device));
     if (device < 0 || device >= kMaxDevices) return fail(PG_ERR_INVALID_ARG, "device %d out of range", device);
+    int params_set = 0;  // the set whose constants this call's kernel uses, read with them
     {
         std::lock_guard<std::mutex> lk(g_mu);
+        params_set = g.params_set;
         if (scratch_ptr[device] == nullptr || consts_gen[device] != g.params_gen) {
             pg_status s = ensure_params();
             if (s != PG_OK) return s;
@@ -2168,7 +2208,7 @@ pg_status pg_merkle_build_noalloc(const uint64_t *rows, size_t n_leaves, size_t 
     const uint32_t cap = (uint32_t)(sm_count[device] * blocks_per_sm[device]);
     const unsigned grid = want < cap ? want : cap;
     ProfScope prof(kIdSingle, st, tree_perms(n_leaves, width));
-    if (g.params_set == 1) dev::k_merkle_single<dev::kMdsSmall><<<grid, dev::kBlock, 0, st>>>(tp, tasks, scratch + 1, scratch);
+    if (params_set == 1) dev::k_merkle_single<dev::kMdsSmall><<<grid, dev::kBlock, 0, st>>>(tp, tasks, scratch + 1, scratch);
     else dev::k_merkle_single<dev::kMdsFull><<<grid, dev::kBlock, 0, st>>>(tp, tasks, scratch + 1, scratch);
     PG_CUDA(cudaGetLastError());
     return PG_OK;

@@ -176,61 +176,103 @@ __device__ __forceinline__ void dense_small_phase(uint64_t *slot, int rows = kT)
 #define PG12_PARTIAL_PAIRS 1
 #endif
 
-template <int S>
+// In the pairs form: 1 sums the dot product's even and odd cells in two
+// accumulators (two independent carry chains), joined before the one
+// reduction; 0 (default): one accumulator.
+#ifndef PG12_PARTIAL_ACC2
+#define PG12_PARTIAL_ACC2 0
+#endif
+
+// Sum of two lazy accumulators (A += B), each below 2^150.
+__device__ __forceinline__ void acc_join(Acc &A, const Acc &B) {
+    asm("add.cc.u32 %0, %0, %5;\n\t"
+        "addc.cc.u32 %1, %1, %6;\n\t"
+        "addc.cc.u32 %2, %2, %7;\n\t"
+        "addc.cc.u32 %3, %3, %8;\n\t"
+        "addc.u32 %4, %4, %9;"
+        : "+r"(A.a0), "+r"(A.a1), "+r"(A.a2), "+r"(A.a3), "+r"(A.a4)
+        : "r"(B.a0), "r"(B.a1), "r"(B.a2), "r"(B.a3), "r"(B.a4));
+#if PG12_ACC_MID64
+    A.mlo += B.mlo;
+    A.mhi += B.mhi;
+#else
+    asm("add.cc.u32 %0, %0, %3;\n\t"
+        "addc.cc.u32 %1, %1, %4;\n\t"
+        "addc.u32 %2, %2, %5;"
+        : "+r"(A.m0), "+r"(A.m1), "+r"(A.m2)
+        : "r"(B.m0), "r"(B.m1), "r"(B.m2));
+#endif
+}
+
+template <int S, int LOOP = PG12_PARTIAL_LOOP>
 __device__ __forceinline__ void partial_phase(uint64_t *slot) {
-#if PG12_PARTIAL_LOOP
-    // Cells 1..11 stay in the slot; each round walks them once, so the loop
-    // body is one cell's product and update instead of all eleven.
+    if (LOOP) {
+        // Cells 1..11 stay in the slot; each round walks them once, so the loop
+        // body is one cell's product and update instead of all eleven.
 #pragma unroll 1
-    for (int q = 0; q < kRP; ++q) {
-        const uint64_t x0 = sbox(add_canon(slot[0], c_dev.part_rc[q]));
-        Acc A;
-        acc_zero(A);
-        acc_mac(A, x0, c_dev.part_v[q][0]);
+        for (int q = 0; q < kRP; ++q) {
+            const uint64_t x0 = sbox(add_canon(slot[0], c_dev.part_rc[q]));
+            Acc A;
+            acc_zero(A);
+            acc_mac(A, x0, c_dev.part_v[q][0]);
 #if PG12_PARTIAL_PAIRS
-        // cell 1, then cells (2,3) ... (10,11) two per iteration
-        {
-            const uint64_t x1 = slot[S];
-            acc_mac(A, x1, c_dev.part_v[q][1]);
-            slot[S] = mul_add(c_dev.part_w[q][1], x0, x1);
-        }
+            // cell 1, then cells (2,3) ... (10,11) two per iteration
+            {
+                const uint64_t x1 = slot[S];
+                acc_mac(A, x1, c_dev.part_v[q][1]);
+                slot[S] = mul_add(c_dev.part_w[q][1], x0, x1);
+            }
+#if PG12_PARTIAL_ACC2
+            Acc B;
+            acc_zero(B);
 #pragma unroll 1
-        for (int j = 2; j < kT; j += 2) {
-            const uint64_t xa = slot[j * S], xb = slot[(j + 1) * S];
-            acc_mac(A, xa, c_dev.part_v[q][j]);
-            acc_mac(A, xb, c_dev.part_v[q][j + 1]);
-            slot[j * S] = mul_add(c_dev.part_w[q][j], x0, xa);
-            slot[(j + 1) * S] = mul_add(c_dev.part_w[q][j + 1], x0, xb);
-        }
+            for (int j = 2; j < kT; j += 2) {
+                const uint64_t xa = slot[j * S], xb = slot[(j + 1) * S];
+                acc_mac(A, xa, c_dev.part_v[q][j]);
+                acc_mac(B, xb, c_dev.part_v[q][j + 1]);
+                slot[j * S] = mul_add(c_dev.part_w[q][j], x0, xa);
+                slot[(j + 1) * S] = mul_add(c_dev.part_w[q][j + 1], x0, xb);
+            }
+            acc_join(A, B);
 #else
 #pragma unroll 1
-        for (int j = 1; j < kT; ++j) {
-            const uint64_t xj = slot[j * S];
-            acc_mac(A, xj, c_dev.part_v[q][j]);
-            slot[j * S] = mul_add(c_dev.part_w[q][j], x0, xj);
-        }
+            for (int j = 2; j < kT; j += 2) {
+                const uint64_t xa = slot[j * S], xb = slot[(j + 1) * S];
+                acc_mac(A, xa, c_dev.part_v[q][j]);
+                acc_mac(A, xb, c_dev.part_v[q][j + 1]);
+                slot[j * S] = mul_add(c_dev.part_w[q][j], x0, xa);
+                slot[(j + 1) * S] = mul_add(c_dev.part_w[q][j + 1], x0, xb);
+            }
 #endif
-        slot[0] = acc_reduce(A);
-    }
 #else
-    uint64_t x[kT];
-#pragma unroll
-    for (int j = 0; j < kT; ++j) x[j] = slot[j * S];
 #pragma unroll 1
-    for (int q = 0; q < kRP; ++q) {
-        const uint64_t x0 = sbox(add_canon(x[0], c_dev.part_rc[q]));
-        Acc A;
-        acc_zero(A);
-        acc_mac(A, x0, c_dev.part_v[q][0]);
-#pragma unroll
-        for (int j = 1; j < kT; ++j) acc_mac(A, x[j], c_dev.part_v[q][j]);
-#pragma unroll
-        for (int i = 1; i < kT; ++i) x[i] = mul_add(c_dev.part_w[q][i], x0, x[i]);
-        x[0] = acc_reduce(A);
-    }
-#pragma unroll
-    for (int j = 0; j < kT; ++j) slot[j * S] = x[j];
+            for (int j = 1; j < kT; ++j) {
+                const uint64_t xj = slot[j * S];
+                acc_mac(A, xj, c_dev.part_v[q][j]);
+                slot[j * S] = mul_add(c_dev.part_w[q][j], x0, xj);
+            }
 #endif
+            slot[0] = acc_reduce(A);
+        }
+    } else {
+        uint64_t x[kT];
+#pragma unroll
+        for (int j = 0; j < kT; ++j) x[j] = slot[j * S];
+#pragma unroll 1
+        for (int q = 0; q < kRP; ++q) {
+            const uint64_t x0 = sbox(add_canon(x[0], c_dev.part_rc[q]));
+            Acc A;
+            acc_zero(A);
+            acc_mac(A, x0, c_dev.part_v[q][0]);
+#pragma unroll
+            for (int j = 1; j < kT; ++j) acc_mac(A, x[j], c_dev.part_v[q][j]);
+#pragma unroll
+            for (int i = 1; i < kT; ++i) x[i] = mul_add(c_dev.part_w[q][i], x0, x[i]);
+            x[0] = acc_reduce(A);
+        }
+#pragma unroll
+        for (int j = 0; j < kT; ++j) slot[j * S] = x[j];
+    }
 }
 
 // Matrix kinds the kernels are compiled for: the full-width Cauchy matrix

@@ -30,7 +30,8 @@ constexpr int kTcAChunk = 128;                // bytes of one 8 x 8 fp16 core ma
 constexpr int kTcAChunks = kTcK / 8;           // core-matrix columns of A (12)
 constexpr int kTcABytes = kTcGroup * kTcK * 2;  // A operand of a group: 24 KiB
 constexpr int kTcSlotBytes = kTcGroup * kT * 8;
-constexpr int kTcTmemCols = 128;              // D needs 96 columns; allocations are powers of two
+constexpr int kTcDCols = kTcN;                // columns of one group's D (96, a multiple of 32)
+constexpr int kTcTmemAlloc = 512;             // one allocation per CTA (a power of two >= the groups' D)
 // instruction descriptor: fp16 A and B, fp32 D, both K-major, N = 96, M = 128
 constexpr uint32_t kTcIdesc = (1u << 4) | ((uint32_t)(kTcN >> 3) << 17) | ((uint32_t)(kTcGroup >> 4) << 24);
 // a wait that has not seen the tensor cores finish after this many SM clocks gives up
@@ -127,7 +128,7 @@ struct TcGroup {
     uint8_t *a;           // A operand, kTcABytes
     uint64_t *slot;       // states: cell i of thread t at slot[i * kTcGroup + t]
     uint64_t *mbar;       // tensor-core completion barrier
-    uint32_t tmem;        // D: lanes 0..127, kTcTmemCols columns
+    uint32_t tmem;        // D: lanes 0..127, kTcDCols columns
     uint32_t phase;       // parity of the mbarrier's next completion
     int bar;              // named barrier of the group's 128 threads
     int t;                // thread index within the group
@@ -186,6 +187,17 @@ __device__ __forceinline__ bool tc_dense(TcGroup &G, int m, bool z, int rows) {
     return true;
 }
 
+// Code shape of the tensor-core path (measured on the 2^22 x 8 tree, 4
+// groups): S-boxes four cells per loop iteration and the partial rounds'
+// eleven cells unrolled in registers, 10.25 ms; two cells per iteration and
+// the cells walked in the slots (the integer-pipe kernels' shape), 10.67 ms.
+#ifndef PG12_TC_SBOX_CELLS
+#define PG12_TC_SBOX_CELLS 4  // 1, 2 or 4 (divides 8 and 12)
+#endif
+#ifndef PG12_TC_PARTIAL_LOOP
+#define PG12_TC_PARTIAL_LOOP 0
+#endif
+
 // The permutation on the group's slots (weak words in, weak words out),
 // with the same zcap / digest shortcuts as permute_slot.
 __device__ __forceinline__ bool tc_permute(TcGroup &G, bool zcap, bool digest) {
@@ -195,14 +207,15 @@ __device__ __forceinline__ bool tc_permute(TcGroup &G, bool zcap, bool digest) {
         const bool z = zcap && r == 0;
         const int cells = z ? kRate : kT;
 #pragma unroll 1
-        for (int j = 0; j < cells; j += 2) {
-            const uint64_t a0 = add_canon(slot[j * kTcGroup], c_dev.full_rc[r][j]);
-            const uint64_t a1 = add_canon(slot[(j + 1) * kTcGroup], c_dev.full_rc[r][j + 1]);
-            tc_put(G, j, sbox(a0));
-            tc_put(G, j + 1, sbox(a1));
+        for (int j = 0; j < cells; j += PG12_TC_SBOX_CELLS) {
+            uint64_t a[PG12_TC_SBOX_CELLS];
+#pragma unroll
+            for (int k = 0; k < PG12_TC_SBOX_CELLS; ++k) a[k] = add_canon(slot[(j + k) * kTcGroup], c_dev.full_rc[r][j + k]);
+#pragma unroll
+            for (int k = 0; k < PG12_TC_SBOX_CELLS; ++k) tc_put(G, j + k, sbox(a[k]));
         }
         if (!tc_dense(G, r == kRF / 2 - 1 ? 1 : 0, z, digest && r == kRF - 1 ? kDigest : kT)) return false;
-        if (r == kRF / 2 - 1) partial_phase<kTcGroup>(slot);
+        if (r == kRF / 2 - 1) partial_phase<kTcGroup, PG12_TC_PARTIAL_LOOP>(slot);
     }
     return true;
 }
@@ -211,6 +224,7 @@ __device__ __forceinline__ bool tc_permute(TcGroup &G, bool zcap, bool digest) {
 // group's A operand, then each group's state slots, then the barriers.
 template <int GROUPS>
 struct TcLayout {
+    static_assert(GROUPS * kTcDCols <= kTcTmemAlloc, "the groups' accumulators exceed tensor memory");
     static constexpr size_t kTables = 0;
     static constexpr size_t kA = (sizeof(TcTables) + 127) & ~(size_t)127;
     static constexpr size_t kSlot = kA + (size_t)GROUPS * kTcABytes;
@@ -237,7 +251,7 @@ __device__ __forceinline__ TcGroup tc_setup(uint8_t *sm) {
     }
     if (threadIdx.x < 32) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tslot)),
-                     "r"(GROUPS * kTcTmemCols));
+                     "r"(kTcTmemAlloc));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     fence_async_smem();
@@ -251,7 +265,7 @@ __device__ __forceinline__ TcGroup tc_setup(uint8_t *sm) {
     G.a = sm + L::kA + (size_t)g * kTcABytes;
     G.slot = reinterpret_cast<uint64_t *>(sm + L::kSlot + (size_t)g * kTcSlotBytes);
     G.mbar = bars + g;
-    G.tmem = *tslot + (uint32_t)(g * kTcTmemCols);
+    G.tmem = *tslot + (uint32_t)(g * kTcDCols);
     G.phase = 0;
     G.bar = 1 + g;
     G.bcast = reinterpret_cast<volatile uint32_t *>(sm + L::kBcast) + g;
@@ -289,7 +303,7 @@ __device__ __forceinline__ void tc_teardown(uint8_t *sm, TcGroup &G) {
     if (threadIdx.x < 32) {
         tc_fence_after();
         const uint32_t base = *reinterpret_cast<uint32_t *>(sm + L::kBar + 8 * GROUPS);
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(base), "r"(GROUPS * kTcTmemCols));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(base), "r"(kTcTmemAlloc));
     }
 }
 

@@ -207,3 +207,51 @@ def test_merkle_on_side_stream():
         nodes = pg.merkle_build(t, stream=s)
     s.synchronize()
     assert (host(nodes) == oracle.merkle_build(rows, nthreads=4)).all()
+
+
+@pytest.mark.parametrize("engine", [pg.ENGINE_TENSOR, pg.ENGINE_INT])
+def test_merkle_builds_on_two_streams_at_once(engine):
+    # two different trees built concurrently on two streams with no
+    # synchronisation between them: the build keeps no shared device state
+    n = 1 << 16
+    a_np = pg_synth.matrix(0xA51, n, 8)
+    b_np = pg_synth.matrix(0xB52, n, 24)
+    a, b = dev(a_np), dev(b_np)
+    sa, sb = torch.cuda.Stream(), torch.cuda.Stream()
+    torch.cuda.synchronize()
+    pg.set_engine(engine)
+    try:
+        outs = []
+        for _ in range(3):
+            with torch.cuda.stream(sa):
+                na = pg.merkle_build(a, stream=sa)
+            with torch.cuda.stream(sb):
+                nb = pg.merkle_build(b, stream=sb)
+            outs.append((na, nb))
+        sa.synchronize()
+        sb.synchronize()
+    finally:
+        pg.set_engine(pg.ENGINE_TENSOR)
+    want_a = oracle.merkle_build(a_np, nthreads=8)
+    want_b = oracle.merkle_build(b_np, nthreads=8)
+    for na, nb in outs:
+        assert (host(na) == want_a).all()
+        assert (host(nb) == want_b).all()
+
+
+def test_merkle_rejects_overlapping_rows_and_nodes():
+    # checked on the host before anything is launched
+    buf = torch.zeros(1 << 16, dtype=torch.int64, device="cuda")
+    rows = buf[: 1024 * 8].view(1024, 8)
+    nodes = buf[4096: 4096 + 2047 * 4].view(2047, 4)
+    with pytest.raises(pg.PGError) as e:
+        pg.merkle_build(rows, nodes)
+    assert e.value.status == 1 and "overlap" in pg.last_error()
+    # two trees of a batch whose node buffers share words
+    ra = torch.zeros((1024, 8), dtype=torch.int64, device="cuda")
+    rb = torch.zeros((1024, 8), dtype=torch.int64, device="cuda")
+    nbuf = torch.zeros(3 * 2047 * 4, dtype=torch.int64, device="cuda")
+    na, nb = nbuf[: 2047 * 4].view(2047, 4), nbuf[4000: 4000 + 2047 * 4].view(2047, 4)
+    with pytest.raises(pg.PGError) as e:
+        pg.merkle_build_batch([ra, rb], nodes_list=[na, nb])
+    assert e.value.status == 1 and "overlap" in pg.last_error()

@@ -9,6 +9,9 @@ process.  The path is exact integer arithmetic, so the tolerance is zero:
 outputs must match word for word.
 """
 import ctypes
+import os
+import subprocess
+import sys
 
 import numpy as np
 import pytest
@@ -75,3 +78,41 @@ def test_noalloc_rejects_more_than_the_limit():
                                                 ctypes.c_void_p(nodes.data_ptr()), None)
     assert status == 1
     assert "limit" in pg.last_error()
+
+
+_FRESH = r"""
+import ctypes, sys
+import numpy as np
+import torch
+sys.path.insert(0, {root!r})
+import oracle, pg_synth
+import paper_2506_09505_gb300 as pg
+lib = pg.load()
+rows_np = pg_synth.matrix(0x44, 1 << 10, 8)
+rows = torch.from_numpy(rows_np.view(np.int64)).cuda()
+nodes = torch.full((2047, 4), -1, dtype=torch.int64, device="cuda")
+# first call of the process: no pg_init() before it
+st = lib.pg_merkle_build_noalloc(ctypes.c_void_p(rows.data_ptr()), 1 << 10, 8,
+                                 ctypes.c_void_p(nodes.data_ptr()), ctypes.c_void_p(0))
+assert st == 0, pg.last_error()
+torch.cuda.synchronize()
+got = nodes.cpu().numpy().view(np.uint64)
+assert (got == oracle.merkle_build(rows_np, nthreads=4)).all()
+# a second call, then the allocating entry point after pg_init, agree
+again = torch.empty_like(nodes)
+assert lib.pg_merkle_build_noalloc(ctypes.c_void_p(rows.data_ptr()), 1 << 10, 8,
+                                   ctypes.c_void_p(again.data_ptr()), ctypes.c_void_p(0)) == 0
+pg.init(0)
+assert torch.equal(again, nodes) and torch.equal(pg.merkle_build(rows), nodes)
+print("fresh-process no-alloc ok")
+"""
+
+
+def test_noalloc_in_a_fresh_process_without_pg_init():
+    # the promise that the entry point needs no pg_init(): its own set-up
+    # (constant tables, scratch address) runs on the first call
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, "-c", _FRESH.format(root=root)], capture_output=True, text=True,
+                         timeout=600, cwd=root)
+    assert out.returncode == 0, out.stdout[-2000:] + out.stderr[-2000:]
+    assert "fresh-process no-alloc ok" in out.stdout
