@@ -55,16 +55,6 @@ LEVEL_KERNELS = ("k_merkle_level", "k_tc_sponge:level")
 LEAF_KERNELS = ("k_merkle", "k_merkle_top_leaf", "k_tc_sponge:leaves")
 IMAD_RESULTS_PER_CLK_SM = 64  # 32-bit multiply results per clock per SM
 L2_BYTES = 129 * 10**6  # GB300 L2
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of each
-# kernel of a tree build, averaged over its launches in one ncu capture of the
-# current kernels on that workload (params, log2 leaves, width); other
-# workloads report null.
-KERNEL_TRAFFIC = {("pg12_v1", 22, 8, "k_merkle"): 373_116_562,
-                  ("pg12_v1", 22, 8, "k_merkle_level"): 37_407_000,
-                  ("pg12_v1", 22, 8, "k_merkle_top"): 173_674,
-                  ("pg12_v1", 22, 8, "k_merkle_top_tail"): 40_554}
-
-
 def algorithmic_bytes(kernel, perms_per_launch, width):
     """Bytes a launch must move: rows read and digests written (leaves), or two
     child digests read and one written per node (levels)."""
@@ -90,6 +80,7 @@ def parse_args():
                          "tree; serve: Poisson stream of tree-build requests; lde: low-degree "
                          "extension of a trace, then its Merkle commitment")
     ap.add_argument("--lde-log-n", type=int, default=21)
+    ap.add_argument("--permute-log-n", type=int, default=24, help="log2 of the states of the permute workload")
     ap.add_argument("--log-blowup", type=int, default=1)
     ap.add_argument("--trees", type=int, default=64)
     ap.add_argument("--requests", type=int, default=2000)
@@ -121,6 +112,32 @@ def measured_peaks():
             return json.load(f)
     except Exception:
         return {}
+
+
+# ------------------------------------------------------------ measured kernel metrics
+METRICS = os.path.join(ROOT, "profiles", "kernel_metrics.json")
+
+
+def kernel_metrics() -> dict:
+    """ncu figures of the current kernels (profiles/kernel_metrics.json): pipe
+    utilisation, instructions per permutation and DRAM bytes per launch.  Empty
+    when the kernel sources changed since they were captured (stale counters
+    are not reported)."""
+    import hashlib
+    try:
+        with open(METRICS) as f:
+            m = json.load(f)
+        h = hashlib.sha256()
+        for rel in m["source_files"]:
+            with open(os.path.join(ROOT, rel), "rb") as f:
+                h.update(f.read())
+        return m if h.hexdigest() == m["source_sha256"] else {}
+    except Exception:
+        return {}
+
+
+def metrics_kernel(name: str) -> str:
+    return name.split(":")[0]
 
 
 # ------------------------------------------------------------ stored oracle results
@@ -442,6 +459,10 @@ def run_ours(args):
         share = 1.0 if name in LEVEL_KERNELS else 1.0 / chunks
         return mul_per_perm - share * saved
 
+    km = kernel_metrics()
+    traffic_table = km.get("traffic_bytes_per_launch", {}).get(f"merkle_2e{args.log_n}_w{args.width}", {}) \
+        if args.params in (None, "pg12_v1") else {}
+
     def kernel_roofline(name):
         v = kernels[name]
         launch_ms = v["total_ms"] / v["launches"]      # average launch, event-timed
@@ -452,12 +473,25 @@ def run_ours(args):
                 "frac_executed": ach_x / peak, "executed_mul32_results_per_perm": executed_per_perm(name),
                 "mul32_results_per_launch": per_launch * mul_per_perm,
                 "algorithmic_bytes_per_launch": algorithmic_bytes(name, per_launch, args.width),
-                "traffic": KERNEL_TRAFFIC.get((args.params or "pg12_v1", args.log_n, args.width, name))}
+                "traffic": traffic_table.get(name)}
 
     dom = max(kernels, key=lambda k: kernels[k]["total_ms"])   # the kernel with the largest share
     rk = kernel_roofline(dom)
+    # which pipe binds, and the issue-slot ceiling, from the kernel's ncu capture
+    kmet = km.get("kernels", {}).get(metrics_kernel(dom))
+    if kmet:
+        busiest = max(kmet["pipes_pct"], key=kmet["pipes_pct"].get)
+        bound = "alu" if busiest in ("alu", "fmaheavy") else busiest
+        issue_ceiling = 128 * sms * max_mhz * 1e6 / kmet["thread_inst_per_perm"]  # perms/s at 4 warp-issues/clk/SM
+        issue = {"thread_inst_per_perm": kmet["thread_inst_per_perm"], "ceiling_perms_per_s": issue_ceiling,
+                 "frac": rk["perms_per_launch"] / (rk["launch_ms"] / 1e3) / issue_ceiling,
+                 "issue_active_pct_ncu": kmet["issue_active_pct"]}
+        bound_basis = (f"ncu on {metrics_kernel(dom)}: pipes busy {kmet['pipes_pct']} (% of peak); the busiest, "
+                       f"'{busiest}', carries the carry arithmetic of the field products")
+    else:
+        bound, issue, bound_basis = "alu", None, "no ncu capture of the current kernel sources"
     roofline = {
-        "bound": "alu", "kernel": dom,
+        "bound": bound, "bound_basis": bound_basis, "issue": issue, "kernel": dom,
         "achieved": rk["achieved"], "peak": peak, "unit": "T mul32-results/s",
         "frac": rk["frac"],
         "frac_executed": rk["frac_executed"],
@@ -590,17 +624,17 @@ def measure_permute(args):
     """Workload 2: 2^24 independent states permuted in place (raw permutation throughput)."""
     torch, pg = _device_setup()
     import pg_synth
-    n = 1 << 24
+    n = 1 << args.permute_log_n
     seed = pg_synth.config_seed(2)
     st = pg_synth.matrix_torch(seed, n, 12, device="cuda")
     # one permutation of the seeded states, checked against the stored oracle output
     pg.permute_batch(st)
     torch.cuda.synchronize()
-    g = goldens().get("permute_2e24")
+    g = goldens().get("permute_2e24") if n == 1 << 24 else None
     exact = (sha256_words(st) == g["states_sha256"]) if g and args.params in (None, "pg12_v1") else None
     ms, clocks = _timed(lambda: pg.permute_batch(st), args.steps, args.warmup)
     rate = n / (ms / 1e3)
-    out = {"workload": "permute 2^24 states in place", "params": args.params or "pg12_v1",
+    out = {"workload": f"permute 2^{args.permute_log_n} states in place", "params": args.params or "pg12_v1",
            "ms": ms, "perms_per_s": rate, "imad_frac": _imad_frac(args, n, ms / 1e3),
            "kernel": "k_tc_permute" if pg.get_engine() == pg.ENGINE_TENSOR else "k_permute",
            "bit_exact": exact, "bit_exact_basis": "SHA-256 of the 2^24 states after one permutation vs the oracle's",
