@@ -177,7 +177,7 @@ const char *pg_params_name(void);
  *                     (fp16 operands, fp32 sums of integers below 2^24) --
  *                     used by pg_permute_batch, pg_hash_rows, the leaves of
  *                     pg_merkle_build / pg_merkle_build_host and their tree
- *                     levels of at least 2^15 nodes.  The default.
+ *                     levels of at least 2^13 nodes.  The default.
  * pg_set_engine applies to launches made after it returns; PG_ERR_INVALID_ARG
  * for any other value.  Host-only.
  */

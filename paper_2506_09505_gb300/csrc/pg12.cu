@@ -250,17 +250,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_permute(uint64_t *__restri
 // tree level (the level below read as rows of its children's 8 words), or
 // pg_hash_rows.  Launched as a dependent launch it may set up while the
 // kernel before it finishes, and reads `rows` only after pdl_wait().
-__global__ void __launch_bounds__(kTcThreads, 1) k_tc_sponge(const uint64_t *__restrict__ rows, uint64_t n, uint64_t w,
-                                                             int vec16, uint64_t *__restrict__ out) {
+// GROUPS = kTcGroups for large launches (one CTA per SM); GROUPS = 1 for
+// launches of few units (81 KB of shared memory and 128 tensor-memory
+// columns per CTA, two CTAs per SM), which spread them over more SMs.
+template <int GROUPS>
+__global__ void __launch_bounds__(kTcGroup * GROUPS, 1) k_tc_sponge(const uint64_t *__restrict__ rows, uint64_t n,
+                                                                    uint64_t w, int vec16, uint64_t *__restrict__ out) {
     extern __shared__ __align__(1024) uint8_t tc_sm[];
     pdl_trigger();
-    TcGroup G = tc_setup<kTcGroups>(tc_sm);
+    TcGroup G = tc_setup<GROUPS>(tc_sm);
     pdl_wait();
     uint64_t *slot = G.slot + G.t;
     const uint64_t units = (n + kTcGroup - 1) / kTcGroup;
-    const uint64_t step = (uint64_t)gridDim.x * kTcGroups;
+    const uint64_t step = (uint64_t)gridDim.x * GROUPS;
     const uint64_t chunks = (w + kRate - 1) / kRate;
-    for (uint64_t u = (uint64_t)blockIdx.x * kTcGroups + threadIdx.x / kTcGroup; u < units; u += step) {
+    for (uint64_t u = (uint64_t)blockIdx.x * GROUPS + threadIdx.x / kTcGroup; u < units; u += step) {
         const uint64_t r = u * kTcGroup + G.t;
         const bool valid = r < n;
         const uint64_t *row = rows + (valid ? r : 0) * w;
@@ -280,7 +284,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_sponge(const uint64_t *__r
             st2(out + kDigest * r + 2, canon(slot[2 * kTcGroup]), canon(slot[3 * kTcGroup]));
         }
     }
-    tc_teardown<kTcGroups>(tc_sm, G);
+    tc_teardown<GROUPS>(tc_sm, G);
 }
 
 // One warp task: lane i of task u at level l hashes node 32u+i of that level
@@ -738,6 +742,17 @@ __global__ void __launch_bounds__(kVerifyBlock) k_merkle_verify(const uint64_t *
 // ================================================================ host side
 namespace {
 
+// tensor engine: tree levels of at least this many nodes use the tensor-core
+// kernel (one-group CTAs while a level has fewer units than the GPU has
+// groups).  Measured on the 2^22 x 8 tree: 2^15 10.25 ms, 2^13 10.11 ms,
+// 2^12 10.14 ms; below that the 16-lane latency form is faster per level.
+#ifndef PG12_TC_MIN_NODES
+#define PG12_TC_MIN_NODES (1ull << 13)
+#endif
+#ifndef PG12_TC_SMALL_TREE
+#define PG12_TC_SMALL_TREE 8192
+#endif
+
 struct Context {
     bool params_ready = false;
     int params_set = 0;  // 0 = pg12_v1, 1 = pg12_small
@@ -757,7 +772,7 @@ struct Context {
     // 1: permutations of batches, rows, leaves and large levels run their full
     // rounds' dense layers on the tensor cores; 0: integer pipes only
     int engine = 1;
-    uint64_t tc_min_nodes = 1ull << 15;  // smallest tree level built by the tensor-core kernel
+    uint64_t tc_min_nodes = PG12_TC_MIN_NODES;  // smallest tree level built by the tensor-core kernel
     cudaStream_t copy_st = nullptr;  // host-row copies of pg_merkle_build_host
     cudaEvent_t host_ev[17] = {};    // one per chunk, plus "previous work done"
 };
@@ -799,13 +814,16 @@ constexpr size_t kWorkspaceBytes = 32u << 20;  // tree plans + arrival counters
 // in one persistent launch: 16.7 against 17.4 ms for a 2^22 x 8 tree on the
 // integer pipes, 10.20 against 10.73 ms with the tensor-core kernel): the
 // tensor-core kernel for levels of at least tc_min_nodes nodes, one thread
-// per node (k_merkle_level) while the level has more than kWideNodes nodes,
-// the 16-lanes-per-state kernel above that.
+// per node (k_merkle_level) while the level has more than kWideNodes nodes
+// (integer engine), the 16-lanes-per-state kernel above that, and one
+// cluster launch for the levels of at most 64 nodes.
 #ifndef PG12_WIDE_NODES
 #define PG12_WIDE_NODES 8192
 #endif
 constexpr uint64_t kWideNodes = PG12_WIDE_NODES;
 constexpr uint64_t kSmallTree = kWideNodes;
+// tensor engine: trees of at most this many leaves run in the 16-lane form
+constexpr uint64_t kTcSmallTree = PG12_TC_SMALL_TREE;
 constexpr size_t kPlanBytes = 4u << 20;        // first part: plans; rest: counters
 
 // ------------------------------------------------------------ launch timing
@@ -1056,10 +1074,13 @@ pg_status launch_tc_sponge(const uint64_t *rows, uint64_t n, uint64_t w, uint64_
                            int kid) {
     if (n == 0) return PG_OK;
     const int vec16 = ((w % 2) == 0 && (reinterpret_cast<uintptr_t>(rows) % 16) == 0) ? 1 : 0;
+    const uint64_t units = (n + dev::kTcGroup - 1) / dev::kTcGroup;
+    // fewer units than the big CTAs' groups on the whole GPU: one group per CTA
+    const bool one = units < (uint64_t)g.sms * dev::kTcGroups;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(tc_grid(n));
-    cfg.blockDim = dim3(dev::kTcThreads);
-    cfg.dynamicSmemBytes = dev::TcL::kBytes;
+    cfg.gridDim = dim3(one ? (unsigned)units : tc_grid(n));
+    cfg.blockDim = dim3(one ? dev::kTcGroup : dev::kTcThreads);
+    cfg.dynamicSmemBytes = one ? dev::TcLayout<1>::kBytes : dev::TcL::kBytes;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -1067,7 +1088,8 @@ pg_status launch_tc_sponge(const uint64_t *rows, uint64_t n, uint64_t w, uint64_
     cfg.attrs = attr;
     cfg.numAttrs = dependent ? 1 : 0;
     ProfScope prof(kid, st, n * ((w + kRate - 1) / kRate));
-    PG_CUDA(cudaLaunchKernelEx(&cfg, dev::k_tc_sponge, rows, n, w, vec16, out));
+    if (one) PG_CUDA(cudaLaunchKernelEx(&cfg, dev::k_tc_sponge<1>, rows, n, w, vec16, out));
+    else PG_CUDA(cudaLaunchKernelEx(&cfg, dev::k_tc_sponge<dev::kTcGroups>, rows, n, w, vec16, out));
     return PG_OK;
 }
 
@@ -1607,7 +1629,10 @@ pg_status pg_init(int device, const char *params_path) {
     s = upload_tables();
     if (s != PG_OK) return s;
     PG_CUDA(cudaFuncSetAttribute(dev::k_tc_permute, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dev::TcL::kBytes));
-    PG_CUDA(cudaFuncSetAttribute(dev::k_tc_sponge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dev::TcL::kBytes));
+    PG_CUDA(cudaFuncSetAttribute(dev::k_tc_sponge<dev::kTcGroups>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)dev::TcL::kBytes));
+    PG_CUDA(cudaFuncSetAttribute(dev::k_tc_sponge<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)dev::TcLayout<1>::kBytes));
     PG_CUDA(cudaFuncSetAttribute(dev::k_tc_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dev::TcL::kBytes));
     {
         const int ns = ntt_upload_constants();
@@ -1728,7 +1753,7 @@ pg_status pg_merkle_build(const uint64_t *rows, size_t n_leaves, size_t width, u
     // nothing but rows and nodes is read or written, so concurrent builds on
     // different streams are independent
     const uint32_t first_top = 1;
-    if ((uint64_t)n_leaves <= kSmallTree) {  // whole tree in the 16-lane form
+    if ((uint64_t)n_leaves <= (g.engine == 1 ? kTcSmallTree : kSmallTree)) {  // whole tree in the 16-lane form
         const uint64_t threads = (uint64_t)n_leaves * 16;
         const unsigned grid = (unsigned)((threads + dev::kTopBlock - 1) / dev::kTopBlock);
         ProfScope prof(kIdMerkleTopLeaf, st, (uint64_t)n_leaves * ((width + kRate - 1) / kRate));

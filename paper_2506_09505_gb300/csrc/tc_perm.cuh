@@ -31,7 +31,11 @@ constexpr int kTcAChunks = kTcK / 8;           // core-matrix columns of A (12)
 constexpr int kTcABytes = kTcGroup * kTcK * 2;  // A operand of a group: 24 KiB
 constexpr int kTcSlotBytes = kTcGroup * kT * 8;
 constexpr int kTcDCols = kTcN;                // columns of one group's D (96, a multiple of 32)
-constexpr int kTcTmemAlloc = 512;             // one allocation per CTA (a power of two >= the groups' D)
+// tensor-memory columns one CTA of `groups` groups allocates: a power of two
+// (at least 32) that holds every group's D
+constexpr int tc_tmem_alloc(int groups) {
+    return groups * kTcDCols <= 128 ? 128 : groups * kTcDCols <= 256 ? 256 : 512;
+}
 // instruction descriptor: fp16 A and B, fp32 D, both K-major, N = 96, M = 128
 constexpr uint32_t kTcIdesc = (1u << 4) | ((uint32_t)(kTcN >> 3) << 17) | ((uint32_t)(kTcGroup >> 4) << 24);
 // a wait that has not seen the tensor cores finish after this many SM clocks gives up
@@ -224,7 +228,8 @@ __device__ __forceinline__ bool tc_permute(TcGroup &G, bool zcap, bool digest) {
 // group's A operand, then each group's state slots, then the barriers.
 template <int GROUPS>
 struct TcLayout {
-    static_assert(GROUPS * kTcDCols <= kTcTmemAlloc, "the groups' accumulators exceed tensor memory");
+    static_assert(GROUPS * kTcDCols <= 512, "the groups' accumulators exceed tensor memory");
+    static constexpr int kTmemCols = tc_tmem_alloc(GROUPS);
     static constexpr size_t kTables = 0;
     static constexpr size_t kA = (sizeof(TcTables) + 127) & ~(size_t)127;
     static constexpr size_t kSlot = kA + (size_t)GROUPS * kTcABytes;
@@ -251,7 +256,7 @@ __device__ __forceinline__ TcGroup tc_setup(uint8_t *sm) {
     }
     if (threadIdx.x < 32) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tslot)),
-                     "r"(kTcTmemAlloc));
+                     "r"(L::kTmemCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     fence_async_smem();
@@ -303,7 +308,7 @@ __device__ __forceinline__ void tc_teardown(uint8_t *sm, TcGroup &G) {
     if (threadIdx.x < 32) {
         tc_fence_after();
         const uint32_t base = *reinterpret_cast<uint32_t *>(sm + L::kBar + 8 * GROUPS);
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(base), "r"(kTcTmemAlloc));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(base), "r"(L::kTmemCols));
     }
 }
 

@@ -53,19 +53,22 @@ def test_build_launches_account_for_every_permutation(log_n, w, engine):
     leaf_kernel = "k_tc_sponge:leaves" if tc else "k_merkle"
     # the leaves in one launch (the persistent or tensor-core kernel above 8,192 leaves,
     # else the 16-lane kernel), then one launch per level: the tensor-core kernel for
-    # levels of at least 2^15 nodes (tensor engine), one thread per node (k_merkle_level)
-    # above 8,192 nodes, else the 16-lane kernel (k_merkle_top)
+    # levels of at least 2^13 nodes (tensor engine), one thread per node (k_merkle_level)
+    # above 8,192 nodes (integer engine), else the 16-lane kernel (k_merkle_top)
     if n > 8192:
         assert got[leaf_kernel]["launches"] == 2 and got[leaf_kernel]["perms"] == 2 * n * ((w + 7) // 8)
     else:
         assert leaf_kernel not in got and got["k_merkle_top_leaf"]["launches"] == 2
-    tc_levels = sum(1 for l in range(1, log_n + 1) if tc and n > 8192 and n >> l >= 1 << 15)
+    levels = [n >> l for l in range(1, log_n + 1)]
+    is_tc = [tc and n > 8192 and c >= 1 << 13 for c in levels]
+    tc_levels = sum(is_tc)
     assert got.get("k_tc_sponge:level", {"launches": 0})["launches"] == 2 * tc_levels
-    per_node = sum(1 for l in range(1, log_n + 1) if n >> l > 8192) - tc_levels
+    per_node = sum(1 for c, t in zip(levels, is_tc) if c > 8192 and not t)
     assert got.get("k_merkle_level", {"launches": 0})["launches"] == 2 * per_node
-    # levels of 65..8,192 nodes: one k_merkle_top launch each; from the first level of at most
-    # 64 nodes up to the root: one k_merkle_top_tail launch (or a lone root: k_merkle_top)
-    mid = sum(1 for l in range(1, log_n + 1) if 64 < n >> l <= 8192)
+    # levels of 65..8,192 nodes not on the tensor cores: one k_merkle_top launch each; from
+    # the first level of at most 64 nodes up to the root: one k_merkle_top_tail launch (or a
+    # lone root: k_merkle_top)
+    mid = sum(1 for c, t in zip(levels, is_tc) if 64 < c <= 8192 and not t)
     tail_first = next((l for l in range(1, log_n + 1) if n >> l <= 64), None)
     if tail_first is not None and tail_first < log_n:
         assert got.get("k_merkle_top_tail", {"launches": 0})["launches"] == 2
