@@ -192,17 +192,37 @@ int pg_get_engine(void);
  * active parameter set, for inspection and CPU tests: with out == NULL
  * returns the table size in bytes; else writes it to `out` (host, `bytes`
  * long) and returns it, or returns 0 if `bytes` is too small.  Layout (all
- * little-endian fp16 bit patterns, K-major 8x8 core matrices of 128 bytes):
- *   b[2][96 rows n = 8i+b][14 chunks]  balanced base-256 digit b of
- *       2^(8a) m_ij mod p at column 8j+a (chunks 0..11; matrix 0 = M of the
- *       full rounds, 1 = round 3's transition matrix), chunk 12 column 0 =
- *       4 u_b (the bias), the rest zero; core matrix (n/8, c) at byte
- *       (n/8 * 14 + c) * 128, row n%8 at 16 (n%8);
- *   a_bias[2 core matrices]  2^-13 at column 0 of every row;
- *   a_zcap[4 core matrices]  bytes of (c_0[j])^7, j = 8..11, every row.
+ * little-endian fp16 bit patterns, K-major 8x8 core matrices of 128 bytes;
+ * a table of n output rows and k input words holds row 8i+b, column 8j+a =
+ * balanced base-256 digit b of 2^(8a) mat[i][j] mod p, core matrix (row
+ * group g, column chunk c) at byte (g k + c) * 128, row r at 16 r):
+ *   m    [96 x 96]  M of the full rounds
+ *   pre  [96 x 96]  the transition matrix of full round 3
+ *   b_bias [2 core matrices]  row b, column 0 = 4 u_b (the bias digits)
+ *   a_bias [2 core matrices]  2^-13 at column 0 of every row
+ *   a_zcap [4 core matrices]  bytes of (c_0[j])^7, j = 8..11, every row
+ *   vpa  [96 x 96]  rows 0..11 of the chain's vp (pg_params_export_chain)
+ *   vpb  [80 x 96]  rows 12..21 of vp
+ *   w1   [96 x 96]  the chain's w, inputs s_0 .. s_11
+ *   w2   [96 x 80]  w, inputs s_12 .. s_21
  * Host-only; works without a GPU.
  */
 size_t pg_tc_tables_export(void *out, size_t bytes);
+
+/*
+ * pg_params_export_chain -- host copy of the unrolled form of the 22 partial
+ * rounds (Alg. 1, MDSPartial) that the tensor-core kernels compute.  With
+ * x^(0) the state entering partial round 0, y3 the S-box outputs of full
+ * round 3 (so x^(0) = pre * y3), c_q cell 0 before partial round q and
+ * s_q = (c_q + part_rc[q])^7:
+ *   c_0 = x^(0)_0;  c_(q+1) = sum_j vp[q*12 + j] y3_j + sum_(r<=q) beta[q*22 + r] s_r;
+ *   after round 21: cell 0 = c_22 = sum_j vp[21*12 + j] y3_j + sum_r w[0*22 + r] s_r,
+ *                   cell i = x^(0)_i + sum_r w[i*22 + r] s_r  (i = 1..11).
+ *   vp    host, 22*12 words;  beta  host, 22*22 words (r <= q used);
+ *   w     host, 12*22 words (row 0 = beta row 21).
+ * Any pointer may be NULL.  Host-only; works without a GPU.
+ */
+pg_status pg_params_export_chain(uint64_t *vp, uint64_t *beta, uint64_t *w);
 
 /*
  * pg_device_faults -- *faults = 1 if a tensor-core kernel launched since the

@@ -97,6 +97,7 @@ SIGNATURES = {
     "pg_params_name": (ctypes.c_char_p, []),
     "pg_set_engine": (ctypes.c_int, [ctypes.c_int]),
     "pg_tc_tables_export": (ctypes.c_size_t, [ctypes.c_void_p, ctypes.c_size_t]),
+    "pg_params_export_chain": (ctypes.c_int, [_u64p, _u64p, _u64p]),
     "pg_get_engine": (ctypes.c_int, []),
     "pg_device_faults": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint32)]),
     "pg_shutdown": (ctypes.c_int, []),
@@ -237,6 +238,16 @@ def set_engine(engine: int) -> None:
 
 def get_engine() -> int:
     return int(load().pg_get_engine())
+
+
+def params_export_chain():
+    """Unrolled partial rounds: (vp[22,12], beta[22,22], w[12,22]) (see include/pg12.h)."""
+    vp = np.zeros((22, T), dtype=np.uint64)
+    beta = np.zeros((22, 22), dtype=np.uint64)
+    w = np.zeros((T, 22), dtype=np.uint64)
+    _check(load().pg_params_export_chain(vp.ctypes.data_as(_u64p), beta.ctypes.data_as(_u64p),
+                                         w.ctypes.data_as(_u64p)))
+    return vp, beta, w
 
 
 def tc_tables_export() -> bytes:

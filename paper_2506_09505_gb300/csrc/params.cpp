@@ -322,15 +322,64 @@ void balanced_digits(uint64_t r, int d[8]) {
 
 }  // namespace
 
-void build_tc_tables(const OptParams &op, TcTables &tt) {
+void derive_chain(const OptParams &op, ChainParams &cp) {
+    std::memset(&cp, 0, sizeof cp);
+    // v_q[i] and w_r[i] for i = 0..11 (w_r[0] unused)
+    auto v = [&](int q, int i) { return op.part_v[q][i] % kP; };
+    auto w = [&](int r, int i) { return op.part_w[r][i - 1] % kP; };
+    for (int q = 0; q < kRP; ++q)
+        for (int j = 0; j < kT; ++j) {
+            uint64_t acc = 0;
+            for (int i = 1; i < kT; ++i) acc = fp_add(acc, fp_mul(v(q, i), op.pre[i][j] % kP));
+            cp.vp[q][j] = acc;
+        }
+    for (int q = 0; q < kRP; ++q) {
+        for (int r = 0; r < q; ++r) {
+            uint64_t acc = 0;
+            for (int i = 1; i < kT; ++i) acc = fp_add(acc, fp_mul(v(q, i), w(r, i)));
+            cp.beta[q][r] = acc;
+        }
+        cp.beta[q][q] = v(q, 0);
+    }
+    for (int r = 0; r < kRP; ++r) {
+        cp.w[0][r] = cp.beta[kRP - 1][r];
+        for (int i = 1; i < kT; ++i) cp.w[i][r] = w(r, i);
+    }
+}
+
+namespace {
+
+// Digit table of an (n x k) matrix mat (row-major, canonical words): output
+// row i, input word j; B operand row 8 i + b, column 8 j + a holds digit b of
+// 2^(8a) mat[i][j].  Records, per output column, the largest positive and
+// negative sums of digits over the table (for the exactness check).
+void digit_table(const uint64_t *mat, int n, int k, uint16_t *dst, long *pos, long *neg) {
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < k; ++j)
+            for (int a = 0; a < 8; ++a) {
+                int d[8];
+                balanced_digits(fp_mul(mat[i * k + j] % kP, fp_pow(2, 8 * (uint64_t)a)), d);
+                for (int b = 0; b < 8; ++b) {
+                    const int row = 8 * i + b;
+                    dst[(row / 8 * k + j) * 64 + (row % 8) * 8 + a] = half_of_int(d[b]);
+                    if (d[b] > 0) pos[row] += d[b];
+                    else neg[row] -= d[b];
+                }
+            }
+}
+
+}  // namespace
+
+bool build_tc_tables(const OptParams &op, TcTables &tt) {
     std::memset(&tt, 0, sizeof tt);
     // Bias digits u_b: column (i, b) reads back bits = 0x3E800000 + magic_b + Z
     // with magic_b = 8192 u_b (A bias 2^-13 times B bias 4 u_b, values scaled by
     // 2^-24), and sum_b 2^(8b) (0x3E800000 + 8192 u_b) = 0 (mod p) is solved for
     // u_b in [1407, 1665], the range that keeps magic_b + Z in [2^23, 2^24) for
-    // |Z| <= 3133440.  The sums sum_b u_b 2^(8b) cover every integer from
-    // 1407 G to 1665 G (G = sum_b 2^(8b); 259 digit values for radix 256), an
-    // interval longer than p, so a solution exists.
+    // |Z| <= 3133440 (96 products of a byte and a digit).  The sums
+    // sum_b u_b 2^(8b) cover every integer from 1407 G to 1665 G (G = sum_b
+    // 2^(8b); 259 digit values for radix 256), an interval longer than p, so a
+    // solution exists.
     typedef unsigned __int128 u128;
     const uint64_t G = 0x0101010101010101ull;
     const uint64_t Gp = G % kP;
@@ -341,35 +390,72 @@ void build_tc_tables(const OptParams &op, TcTables &tt) {
     u128 rest = fp_sub(t, umin_p);                               // U - umin, in [0, p)
     int u[8];
     for (int b = 7; b >= 0; --b) {
-        const u128 w = (u128)1 << (8 * b);
-        u128 e = rest / w;
+        const u128 wgt = (u128)1 << (8 * b);
+        u128 e = rest / wgt;
         if (e > 258) e = 258;
-        rest -= e * w;
+        rest -= e * wgt;
         u[b] = 1407 + (int)e;
     }
-    for (int m = 0; m < 2; ++m) {
-        uint16_t *B = tt.b[m];
-        for (int i = 0; i < kT; ++i)
-            for (int j = 0; j < kT; ++j) {
-                const uint64_t mij = (m == 0 ? op.mds[i][j] : op.pre[i][j]) % kP;
-                for (int a = 0; a < 8; ++a) {
-                    int d[8];
-                    balanced_digits(fp_mul(mij, fp_pow(2, 8 * (uint64_t)a)), d);
-                    for (int b = 0; b < 8; ++b) {
-                        const int n = 8 * i + b, c = j;  // k = 8 j + a: chunk j, column a
-                        B[(n / 8 * kTcKC + c) * 64 + (n % 8) * 8 + a] = half_of_int(d[b]);
-                    }
-                }
-            }
-        for (int n = 0; n < kTcN; ++n) B[(n / 8 * kTcKC + 12) * 64 + (n % 8) * 8] = half_of_int(4 * u[n % 8]);
-    }
+    for (int b = 0; b < 8; ++b) tt.b_bias[b * 8] = half_of_int(4 * u[b]);
     for (int r = 0; r < 8; ++r) tt.a_bias[r * 8] = 0x0800;  // 2^-13
+
+    ChainParams cp;
+    derive_chain(op, cp);
+    static uint64_t m[kT * kT], pre[kT * kT], vpa[kT * kT], vpb[kTcUb * kT], w1[kT * kT], w2[kT * kTcW2];
+    for (int i = 0; i < kT; ++i)
+        for (int j = 0; j < kT; ++j) {
+            m[i * kT + j] = op.mds[i][j] % kP;
+            pre[i * kT + j] = op.pre[i][j] % kP;
+            vpa[i * kT + j] = cp.vp[i][j];
+            w1[i * kT + j] = cp.w[i][j];
+        }
+    for (int i = 0; i < kTcUb; ++i)
+        for (int j = 0; j < kT; ++j) vpb[i * kT + j] = cp.vp[kT + i][j];
+    for (int i = 0; i < kT; ++i)
+        for (int j = 0; j < kTcW2; ++j) w2[i * kTcW2 + j] = cp.w[i][kT + j];
+    // every accumulation's worst sums: magic_b - 255 neg >= 2^23 and
+    // magic_b + 255 pos < 2^24 for each column; the final cells accumulate
+    // the two W tables into one sum
+    bool ok = true;
+    auto check = [&](const long *pos, const long *neg, int rows) {
+        for (int r = 0; r < rows; ++r) {
+            const long magic = 8192L * u[r % 8];
+            ok = ok && magic - 255 * neg[r] >= (1L << 23) && magic + 255 * pos[r] < (1L << 24);
+        }
+    };
+    {
+        long pos[kTcN] = {}, neg[kTcN] = {};
+        digit_table(m, kT, kT, tt.m, pos, neg);
+        check(pos, neg, kTcN);
+    }
+    {
+        long pos[kTcN] = {}, neg[kTcN] = {};
+        digit_table(pre, kT, kT, tt.pre, pos, neg);
+        check(pos, neg, kTcN);
+    }
+    {
+        long pos[kTcN] = {}, neg[kTcN] = {};
+        digit_table(vpa, kT, kT, tt.vpa, pos, neg);
+        check(pos, neg, kTcN);
+    }
+    {
+        long pos[kTcN] = {}, neg[kTcN] = {};
+        digit_table(vpb, kTcUb, kT, tt.vpb, pos, neg);
+        check(pos, neg, kTcUb * 8);
+    }
+    {
+        long pos[kTcN] = {}, neg[kTcN] = {};
+        digit_table(w1, kT, kT, tt.w1, pos, neg);
+        digit_table(w2, kT, kTcW2, tt.w2, pos, neg);
+        check(pos, neg, kTcN);
+    }
     for (int j = kRate; j < kT; ++j) {
         const uint64_t c = op.full_rc[0][j] % kP;
         const uint64_t c7 = fp_pow(c, 7);
         for (int r = 0; r < 8; ++r)
             for (int a = 0; a < 8; ++a) tt.a_zcap[(j - kRate) * 64 + r * 8 + a] = (uint16_t)((c7 >> (8 * a)) & 0xFF);
     }
+    return ok;
 }
 
 // ------------------------------------------------------------ SHA-256

@@ -197,70 +197,73 @@ __global__ void __launch_bounds__(kSmallBlock) k_merkle_level(const uint64_t *__
 
 // ------------------------------------------------- tensor-core kernels
 // Persistent kernels of kTcGroups groups of 128 threads (one CTA per SM:
-// with four groups its tables, operands and slots take 187 KB of shared
-// memory and its groups 384 of the 512 columns of tensor memory).  Group q of CTA c takes units
-// c * kTcGroups + q, then every gridDim.x * kTcGroups-th after: a static
-// schedule with no shared counter, so launches on different streams are
-// independent.  A unit is 128 consecutive states or rows; rows past the end
-// are computed on zeros and not stored.
-#ifndef PG12_TC_GROUPS
-#define PG12_TC_GROUPS 4  // groups per CTA: 4 (16 warps) or 5 (20 warps, 223 KB of shared memory; measured 1.3% slower)
+// its tables and operands take 199 KB of shared memory, its groups 128
+// columns of tensor memory each; every thread keeps its state in registers).
+// Group q of CTA c takes units c * kTcGroups + q, then every
+// gridDim.x * kTcGroups-th after: a static schedule with no shared counter,
+// so launches on different streams are independent.  A unit is 128
+// consecutive states or rows; rows past the end are computed on zeros and
+// not stored.
+// PG12_TC_CHAIN 1 (default): the partial rounds in their unrolled form on the
+// tensor cores (tc_partial, 105 KB of tables); 0: on the integer pipes.
+#ifndef PG12_TC_CHAIN
+#define PG12_TC_CHAIN 1
 #endif
+#ifndef PG12_TC_GROUPS
+#define PG12_TC_GROUPS 4
+#endif
+constexpr bool kTcChain = PG12_TC_CHAIN != 0;
 constexpr int kTcGroups = PG12_TC_GROUPS;
 constexpr int kTcThreads = kTcGroup * kTcGroups;
-using TcL = TcLayout<kTcGroups>;
+using TcL = TcLayout<kTcGroups, kTcChain>;
+using TcL1 = TcLayout<1, false>;  // one-group CTAs of small launches
 
 __global__ void __launch_bounds__(kTcThreads, 1) k_tc_permute(uint64_t *__restrict__ st, uint64_t n, int vec16) {
     extern __shared__ __align__(1024) uint8_t tc_sm[];
-    TcGroup G = tc_setup<kTcGroups>(tc_sm);
-    uint64_t *slot = G.slot + G.t;
+    TcGroup G = tc_setup<kTcGroups, kTcChain>(tc_sm);
     const uint64_t units = (n + kTcGroup - 1) / kTcGroup;
     const uint64_t step = (uint64_t)gridDim.x * kTcGroups;
     for (uint64_t u = (uint64_t)blockIdx.x * kTcGroups + threadIdx.x / kTcGroup; u < units; u += step) {
         const uint64_t k = u * kTcGroup + G.t;
         const bool valid = k < n;
         uint64_t *p = st + kT * k;
+        uint64_t x[kT];
         if (valid && vec16) {
 #pragma unroll
-            for (int i = 0; i < kT; i += 2) {
-                uint64_t a, b;
-                ld2_nc(p + i, a, b);
-                slot[i * kTcGroup] = a;
-                slot[(i + 1) * kTcGroup] = b;
-            }
+            for (int i = 0; i < kT; i += 2) ld2_nc(p + i, x[i], x[i + 1]);
         } else {
 #pragma unroll
-            for (int i = 0; i < kT; ++i) slot[i * kTcGroup] = valid ? p[i] : 0ull;
+            for (int i = 0; i < kT; ++i) x[i] = valid ? p[i] : 0ull;
         }
-        if (!tc_permute(G, false, false)) break;
+        if (!tc_permute<kTcChain>(G, x, false, false)) break;
         if (valid) {
             if (vec16) {
 #pragma unroll
-                for (int i = 0; i < kT; i += 2) st2(p + i, canon(slot[i * kTcGroup]), canon(slot[(i + 1) * kTcGroup]));
+                for (int i = 0; i < kT; i += 2) st2(p + i, canon(x[i]), canon(x[i + 1]));
             } else {
 #pragma unroll
-                for (int i = 0; i < kT; ++i) p[i] = canon(slot[i * kTcGroup]);
+                for (int i = 0; i < kT; ++i) p[i] = canon(x[i]);
             }
         }
     }
-    tc_teardown<kTcGroups>(tc_sm, G);
+    tc_teardown<kTcGroups, kTcChain>(tc_sm, G);
 }
 
 // Sponge digests of n rows of width w (Sec. 2.4): the leaves of a tree, or a
 // tree level (the level below read as rows of its children's 8 words), or
 // pg_hash_rows.  Launched as a dependent launch it may set up while the
 // kernel before it finishes, and reads `rows` only after pdl_wait().
-// GROUPS = kTcGroups for large launches (one CTA per SM); GROUPS = 1 for
-// launches of few units (81 KB of shared memory and 128 tensor-memory
-// columns per CTA, two CTAs per SM), which spread them over more SMs.
-template <int GROUPS>
+// GROUPS = kTcGroups for large launches (one CTA per SM); GROUPS = 1 with
+// the partial rounds on the integer pipes for launches of few units (62 KB
+// of shared memory and 128 tensor-memory columns per CTA, up to three CTAs
+// per SM), which spread them over more SMs.
+template <int GROUPS, bool CHAIN>
 __global__ void __launch_bounds__(kTcGroup * GROUPS, 1) k_tc_sponge(const uint64_t *__restrict__ rows, uint64_t n,
                                                                     uint64_t w, int vec16, uint64_t *__restrict__ out) {
     extern __shared__ __align__(1024) uint8_t tc_sm[];
     pdl_trigger();
-    TcGroup G = tc_setup<GROUPS>(tc_sm);
+    TcGroup G = tc_setup<GROUPS, CHAIN>(tc_sm);
     pdl_wait();
-    uint64_t *slot = G.slot + G.t;
     const uint64_t units = (n + kTcGroup - 1) / kTcGroup;
     const uint64_t step = (uint64_t)gridDim.x * GROUPS;
     const uint64_t chunks = (w + kRate - 1) / kRate;
@@ -268,23 +271,24 @@ __global__ void __launch_bounds__(kTcGroup * GROUPS, 1) k_tc_sponge(const uint64
         const uint64_t r = u * kTcGroup + G.t;
         const bool valid = r < n;
         const uint64_t *row = rows + (valid ? r : 0) * w;
+        uint64_t x[kT];
 #pragma unroll
-        for (int i = kRate; i < kT; ++i) slot[i * kTcGroup] = 0;
+        for (int i = kRate; i < kT; ++i) x[i] = 0;
         bool ok = true;
         for (uint64_t c = 0; c < chunks && ok; ++c) {
             uint64_t ch[kRate];
             load_chunk(row, w, c, vec16 != 0, ch);
 #pragma unroll
-            for (int i = 0; i < kRate; ++i) slot[i * kTcGroup] = valid ? ch[i] : 0ull;
-            ok = tc_permute(G, c == 0, c + 1 == chunks);
+            for (int i = 0; i < kRate; ++i) x[i] = valid ? ch[i] : 0ull;
+            ok = tc_permute<CHAIN>(G, x, c == 0, c + 1 == chunks);
         }
         if (!ok) break;
         if (valid) {
-            st2(out + kDigest * r, canon(slot[0]), canon(slot[kTcGroup]));
-            st2(out + kDigest * r + 2, canon(slot[2 * kTcGroup]), canon(slot[3 * kTcGroup]));
+            st2(out + kDigest * r, canon(x[0]), canon(x[1]));
+            st2(out + kDigest * r + 2, canon(x[2]), canon(x[3]));
         }
     }
-    tc_teardown<GROUPS>(tc_sm, G);
+    tc_teardown<GROUPS, CHAIN>(tc_sm, G);
 }
 
 // One warp task: lane i of task u at level l hashes node 32u+i of that level
@@ -433,9 +437,9 @@ __device__ __forceinline__ bool tc_unit(TcGroup &G, const TreePlan &tp, uint32_t
     const uint64_t n = tp.n_leaves, cnt = n >> l;
     const uint64_t k = u * kTcGroup + G.t;
     const bool valid = k < cnt;
-    uint64_t *slot = G.slot + G.t;
+    uint64_t x[kT];
 #pragma unroll
-    for (int i = kRate; i < kT; ++i) slot[i * kTcGroup] = 0;
+    for (int i = kRate; i < kT; ++i) x[i] = 0;
     if (l == 0) {
         const uint64_t w = tp.width, chunks = (w + kRate - 1) / kRate;
         const uint64_t *row = tp.rows + (valid ? k : 0) * w;
@@ -443,24 +447,19 @@ __device__ __forceinline__ bool tc_unit(TcGroup &G, const TreePlan &tp, uint32_t
             uint64_t ch[kRate];
             load_chunk(row, w, c, tp.vec16 != 0, ch);
 #pragma unroll
-            for (int i = 0; i < kRate; ++i) slot[i * kTcGroup] = valid ? ch[i] : 0ull;
-            if (!tc_permute(G, c == 0, c + 1 == chunks)) return false;
+            for (int i = 0; i < kRate; ++i) x[i] = valid ? ch[i] : 0ull;
+            if (!tc_permute<kTcChain>(G, x, c == 0, c + 1 == chunks)) return false;
         }
     } else {
         const uint64_t *kids = tp.nodes + kDigest * (level_off(n, l - 1) + 2 * (valid ? k : 0));
 #pragma unroll
-        for (int i = 0; i < 2 * kDigest; i += 2) {
-            uint64_t a, b;
-            ld2_cg(kids + i, a, b);
-            slot[i * kTcGroup] = a;
-            slot[(i + 1) * kTcGroup] = b;
-        }
-        if (!tc_permute(G, true, true)) return false;
+        for (int i = 0; i < 2 * kDigest; i += 2) ld2_cg(kids + i, x[i], x[i + 1]);
+        if (!tc_permute<kTcChain>(G, x, true, true)) return false;
     }
     if (valid) {
         uint64_t *dst = tp.nodes + kDigest * (level_off(n, l) + k);
-        st2(dst, canon(slot[0]), canon(slot[kTcGroup]));
-        st2(dst + 2, canon(slot[2 * kTcGroup]), canon(slot[3 * kTcGroup]));
+        st2(dst, canon(x[0]), canon(x[1]));
+        st2(dst + 2, canon(x[2]), canon(x[3]));
     }
     return true;
 }
@@ -470,7 +469,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_batch(const TreePlan *__re
                                                             uint32_t *__restrict__ counters,
                                                             uint32_t *__restrict__ next_task) {
     extern __shared__ __align__(1024) uint8_t tc_sm[];
-    TcGroup G = tc_setup<kTcGroups>(tc_sm);
+    TcGroup G = tc_setup<kTcGroups, kTcChain>(tc_sm);
     bool ok = true;
     while (ok) {
         const uint32_t task = group_fetch_add(G, next_task);
@@ -514,7 +513,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_batch(const TreePlan *__re
             lo >>= 1;
         }
     }
-    tc_teardown<kTcGroups>(tc_sm, G);
+    tc_teardown<kTcGroups, kTcChain>(tc_sm, G);
 }
 
 // The top levels of every tree of a batch whose persistent launch stopped
@@ -896,9 +895,14 @@ pg_status upload_tables() {
     dev::make_dev_consts(g.opt, dc);
     PG_CUDA(cudaMemcpyToSymbol(dev::c_dev, &dc, sizeof(dc)));
     PG_CUDA(cudaMemcpyToSymbol(dev::g_dev, &dc, sizeof(dc)));
-    static TcTables tt;  // 43 KB; built under g_mu
-    host::build_tc_tables(g.opt, tt);
+    static TcTables tt;  // 105 KB; built under g_mu
+    if (!host::build_tc_tables(g.opt, tt))
+        return fail(PG_ERR_PARAMS, "parameter set %s: a tensor-core sum could leave the exact fp32 window",
+                    g.params_set == 1 ? "pg12_small" : "pg12_v1");
     PG_CUDA(cudaMemcpyToSymbol(dev::g_tc, &tt, sizeof(tt)));
+    static ChainParams cp;
+    host::derive_chain(g.opt, cp);
+    PG_CUDA(cudaMemcpyToSymbol(dev::c_beta, cp.beta, sizeof(cp.beta)));
     return PG_OK;
 }
 
@@ -1080,7 +1084,7 @@ pg_status launch_tc_sponge(const uint64_t *rows, uint64_t n, uint64_t w, uint64_
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(one ? (unsigned)units : tc_grid(n));
     cfg.blockDim = dim3(one ? dev::kTcGroup : dev::kTcThreads);
-    cfg.dynamicSmemBytes = one ? dev::TcLayout<1>::kBytes : dev::TcL::kBytes;
+    cfg.dynamicSmemBytes = one ? dev::TcL1::kBytes : dev::TcL::kBytes;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -1088,8 +1092,8 @@ pg_status launch_tc_sponge(const uint64_t *rows, uint64_t n, uint64_t w, uint64_
     cfg.attrs = attr;
     cfg.numAttrs = dependent ? 1 : 0;
     ProfScope prof(kid, st, n * ((w + kRate - 1) / kRate));
-    if (one) PG_CUDA(cudaLaunchKernelEx(&cfg, dev::k_tc_sponge<1>, rows, n, w, vec16, out));
-    else PG_CUDA(cudaLaunchKernelEx(&cfg, dev::k_tc_sponge<dev::kTcGroups>, rows, n, w, vec16, out));
+    if (one) PG_CUDA(cudaLaunchKernelEx(&cfg, dev::k_tc_sponge<1, false>, rows, n, w, vec16, out));
+    else PG_CUDA(cudaLaunchKernelEx(&cfg, dev::k_tc_sponge<dev::kTcGroups, dev::kTcChain>, rows, n, w, vec16, out));
     return PG_OK;
 }
 
@@ -1591,6 +1595,18 @@ size_t pg_tc_tables_export(void *out, size_t bytes) {
     return sizeof(TcTables);
 }
 
+pg_status pg_params_export_chain(uint64_t *vp, uint64_t *beta, uint64_t *w) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    pg_status s = ensure_params();
+    if (s != PG_OK) return s;
+    ChainParams cp;
+    host::derive_chain(g.opt, cp);
+    if (vp) std::memcpy(vp, cp.vp, sizeof cp.vp);
+    if (beta) std::memcpy(beta, cp.beta, sizeof cp.beta);
+    if (w) std::memcpy(w, cp.w, sizeof cp.w);
+    return PG_OK;
+}
+
 pg_status pg_set_engine(int engine) {
     if (engine != PG_ENGINE_INT && engine != PG_ENGINE_TENSOR)
         return fail(PG_ERR_INVALID_ARG, "unknown engine %d (0: integer pipes, 1: tensor-core dense layers)", engine);
@@ -1629,10 +1645,10 @@ pg_status pg_init(int device, const char *params_path) {
     s = upload_tables();
     if (s != PG_OK) return s;
     PG_CUDA(cudaFuncSetAttribute(dev::k_tc_permute, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dev::TcL::kBytes));
-    PG_CUDA(cudaFuncSetAttribute(dev::k_tc_sponge<dev::kTcGroups>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)dev::TcL::kBytes));
-    PG_CUDA(cudaFuncSetAttribute(dev::k_tc_sponge<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)dev::TcLayout<1>::kBytes));
+    PG_CUDA(cudaFuncSetAttribute(dev::k_tc_sponge<dev::kTcGroups, dev::kTcChain>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dev::TcL::kBytes));
+    PG_CUDA(cudaFuncSetAttribute(dev::k_tc_sponge<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)dev::TcL1::kBytes));
     PG_CUDA(cudaFuncSetAttribute(dev::k_tc_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dev::TcL::kBytes));
     {
         const int ns = ntt_upload_constants();
@@ -1784,6 +1800,16 @@ pg_status pg_merkle_build(const uint64_t *rows, size_t n_leaves, size_t width, u
     return PG_OK;
 }
 
+// Host-row builds: the first copied chunk holds n / FIRST_DIV rows, each next
+// one twice as many, up to n / MAX_DIV; the 16th takes the rest.
+#ifndef PG12_HOST_CHUNK_FIRST_DIV
+#define PG12_HOST_CHUNK_FIRST_DIV 64
+#endif
+#ifndef PG12_HOST_CHUNK_MAX_DIV
+#define PG12_HOST_CHUNK_MAX_DIV 8
+#endif
+static_assert(PG12_HOST_CHUNK_FIRST_DIV >= PG12_HOST_CHUNK_MAX_DIV, "host chunks: the first is the smallest");
+
 pg_status pg_merkle_build_host(const uint64_t *rows_host, size_t n_leaves, size_t width, uint64_t *rows_dev,
                                uint64_t *nodes, uint64_t *root_out, void *stream) {
     pg_status s = require_init();
@@ -1812,10 +1838,11 @@ pg_status pg_merkle_build_host(const uint64_t *rows_host, size_t n_leaves, size_
     // earlier build may still read it).
     PG_CUDA(cudaEventRecord(g.host_ev[16], st));
     PG_CUDA(cudaStreamWaitEvent(g.copy_st, g.host_ev[16], 0));
-    const uint64_t chunk_max = n / 8;
-    uint64_t chunk = n / 64, first = 0;
+    const uint64_t chunk_max = n / PG12_HOST_CHUNK_MAX_DIV;
+    uint64_t chunk = n / PG12_HOST_CHUNK_FIRST_DIV, first = 0;
     for (uint32_t c = 0; first < n; ++c) {
-        const uint64_t rows_c = chunk < n - first ? chunk : n - first;
+        // the 16th chunk takes whatever is left (16 copy events)
+        const uint64_t rows_c = (chunk < n - first && c < 15) ? chunk : n - first;
         PG_CUDA(cudaMemcpyAsync(rows_dev + first * width, rows_host + first * width, rows_c * bytes_per_row,
                                 cudaMemcpyHostToDevice, g.copy_st));
         PG_CUDA(cudaEventRecord(g.host_ev[c], g.copy_st));

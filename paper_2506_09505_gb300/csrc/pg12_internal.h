@@ -32,35 +32,62 @@ struct OptParams {
     uint64_t part_w[kRP][kT - 1]; // new_i = x_i + w[i-1] x_0
 };
 
-// Tensor-core form of the full rounds' dense layers (Alg. 1, MDS).  Each
-// S-box output x_j is split into its eight bytes x_ja (a = 0..7), each an
-// fp16 operand; each constant (2^(8a) m_ij mod p), taken in (-2^63, 2^63),
-// is split into eight balanced base-256 digits d_ijab in [-128, 127].  Then
-//   y_i = sum_b 2^(8b) Z_ib  (mod p),   Z_ib = sum_(j,a) x_ja d_ijab,
-// a 128 x 96 x 96 product per 128 states whose fp32 sums are exact integers
-// (|Z| <= 96 * 255 * 128 < 2^22).  A bias row adds magic_b to column (i, b)
-// so that every sum lies in [2^23, 2^24), where its fp32 bits are an
-// integer offset of its value, and the magics are chosen so that the offsets
-// cancel mod p: y_i = sum_b 2^(8b) bits(i, b) (mod p).
+// The partial rounds (Alg. 1, MDSPartial) unrolled.  With x^(0) the state
+// entering partial round 0, c_q its cell 0 before round q and
+// s_q = S(c_q + k_q), round q adds w_q[i] s_q to cell i >= 1 and sets cell 0
+// to <v_q, x>, so
+//   x_i^(q) = x_i^(0) + sum_(r<q) w_r[i] s_r                       (i >= 1)
+//   c_(q+1) = U_q + sum_(r<=q) beta[q][r] s_r,  U_q = sum_(i>=1) v_q[i] x_i^(0),
+//   beta[q][r] = sum_(i>=1) v_q[i] w_r[i] (r < q),  beta[q][q] = v_q[0],
+// and after round 21 cell 0 is c_22 and cell i >= 1 is
+// x_i^(0) + sum_r w_r[i] s_r.  Since x^(0) = P y3 (y3 the S-box outputs of
+// full round 3, P its transition matrix), U = (V' P) y3 with V'[q][i] = v_q[i]
+// for i >= 1 and 0 for i = 0.  Only the chain c_q -> s_q -> c_(q+1) is
+// sequential; U and the final updates are two contractions per state.
+struct ChainParams {
+    uint64_t vp[kRP][kT];    // U_q = sum_j vp[q][j] y3_j
+    uint64_t beta[kRP][kRP]; // beta[q][r], r <= q
+    uint64_t w[kT][kRP];     // row 0: beta[21][r]; row i >= 1: w_r[i]
+};
+
+// Tensor-core form of the dense contractions.  Each operand word y_j (a weak
+// 64-bit word) is split into its eight bytes y_ja (a = 0..7), each an fp16
+// operand; each constant (2^(8a) m_ij mod p), taken in [-128 G, 127 G] with
+// G = (2^64 - 1) / 255, is split into eight balanced base-256 digits
+// d_ijab in [-128, 127].  Then
+//   (M y)_i = sum_b 2^(8b) Z_ib  (mod p),   Z_ib = sum_(j,a) y_ja d_ijab,
+// a 128 x 8K x 8N product per 128 states whose fp32 sums are exact
+// integers.  A bias block adds magic_b to column (i, b) so that every sum
+// lies in [2^23, 2^24) (times 2^-24), where its fp32 bits are an integer
+// offset of its value, and the magics are chosen so that the offsets cancel
+// mod p: (M y)_i = sum_b 2^(8b) bits(i, b) (mod p).
 //
-// The operands are stored in the tensor cores' K-major, unswizzled layout:
-// 8 x 8 fp16 "core matrices" of 128 contiguous bytes, row r at 16 r.
-constexpr int kTcN = kT * 8;       // output columns (i, b)
-constexpr int kTcK = kT * 8;       // data K (j, a)
-constexpr int kTcKC = kTcK / 8 + 2;  // core-matrix columns of a B table: 12 data + 2 bias
+// Operands are stored in the tensor cores' K-major, unswizzled layout: 8 x 8
+// fp16 "core matrices" of 128 contiguous bytes, row r at 16 r.  A table of
+// N = 8 n rows (outputs) and K = 8 k columns (input words) holds core matrix
+// (row group g, column chunk c) at halfs (g k + c) * 64.
+constexpr int kTcN = kT * 8;   // output columns (i, b) of a 12-row table
+constexpr int kTcK = kT * 8;   // K of a 12-word input
+constexpr int kTcUb = kRP - kT;  // rows of the second U table (U_12 .. U_21)
+constexpr int kTcW2 = kRP - kT;  // input words of the second W table (s_12 .. s_21)
 struct TcTables {
-    // B operand of matrix m (0: M of the full rounds, 1: the transition matrix
-    // of round 3): row n = 8 i + b, column k = 8 j + a (12 data chunks), then
-    // the bias chunks (column 96 = 4 u_b, the rest 0); core matrix (n/8, c)
-    // at halfs (n/8 * kTcKC + c) * 64.
-    uint16_t b[2][kTcN * kTcKC * 8];
-    // A operand of the bias: 8 identical rows (read with a zero row-group
-    // stride), 2^-13 at column 0; two core matrices.
+    // the part every tensor-core kernel copies (full rounds)
+    uint16_t m[kTcN * kTcK];          // M of the full rounds
+    uint16_t pre[kTcN * kTcK];        // transition matrix of full round 3
+    // B operand of the bias: 8 rows b (the same for every row group: read with
+    // a zero row-group stride), column 0 = 4 u_b, the rest 0; two core matrices
+    uint16_t b_bias[2 * 64];
+    // A operand of the bias: 8 identical rows, 2^-13 at column 0
     uint16_t a_bias[2 * 64];
     // A operand of cells 8..11 in round 0 of a state whose capacity enters as
     // zero: the bytes of (c_0[j])^7 as fp16 subnormals, 8 identical rows per
-    // core matrix, one core matrix per cell.
+    // core matrix, one core matrix per cell
     uint16_t a_zcap[4 * 64];
+    // the partial rounds' contractions (ChainParams)
+    uint16_t vpa[kTcN * kTcK];        // U_0 .. U_11 from y3
+    uint16_t vpb[kTcUb * 8 * kTcK];   // U_12 .. U_21 from y3 (80 rows)
+    uint16_t w1[kTcN * kTcK];         // final cells from s_0 .. s_11
+    uint16_t w2[kTcN * kTcW2 * 8];    // final cells from s_12 .. s_21 (80 columns)
 };
 static_assert(sizeof(TcTables) % 16 == 0, "tables are copied in 16-byte pieces");
 
@@ -109,8 +136,11 @@ void generate_plain(PlainParams &pp);
 // candidate's index.
 int generate_small(PlainParams &pp, uint32_t row[kT]);
 bool derive_optimized(const PlainParams &pp, OptParams &op);
-// Digit tables of the tensor-core dense layers for an optimised set.
-void build_tc_tables(const OptParams &op, TcTables &tt);
+// Chain form of the partial rounds of an optimised set.
+void derive_chain(const OptParams &op, ChainParams &cp);
+// Digit tables of the tensor-core contractions for an optimised set; false if
+// a sum could leave the exact window (every table is checked).
+bool build_tc_tables(const OptParams &op, TcTables &tt);
 // FIPS 180-4 SHA-256 of `len` bytes as 64 lowercase hex digits.
 void sha256_hex(const uint8_t *data, size_t len, char out[65]);
 }  // namespace host

@@ -1,47 +1,65 @@
-// Poseidon-12 permutation with the full rounds' dense layers on the tensor
-// cores (tcgen05, sm_103a), 128 states per group of 128 threads.
+// Poseidon-12 permutation with its dense contractions on the tensor cores
+// (tcgen05, sm_103a), 128 states per group of 128 threads.
 //
-// Alg. 1's full rounds are x <- M S(x + c_r).  The S-boxes and the partial
-// rounds stay on the integer pipes (one thread per state, as in
-// poseidon.cuh); the 12x12 products M y of a whole group are one tensor-core
-// contraction of byte limbs (the digit scheme of TcTables in
-// pg12_internal.h):
+// Alg. 1's full rounds are x <- M S(x + c_r); the 12x12 products M y of a
+// whole group are one tensor-core contraction of byte limbs (the digit scheme
+// of TcTables in pg12_internal.h):
 //
 //   thread t: y_j = S(x_j + c_rj), its 8 bytes -> row t of A (fp16
 //             subnormals, bits = byte), in shared memory
-//   leader  : D[128 x 96] = A[128 x 96] * B_m^T + bias   (7 tcgen05.mma, K = 16
+//   leader  : D[128 x 96] = A[128 x 96] * B^T + bias   (7 tcgen05.mma, K = 16
 //             each, fp32 accumulators in tensor memory), commit -> mbarrier
 //   thread t: reads row t of D (tcgen05.ld), y_i = sum_b 2^(8b) bits(D[t][8i+b])
 //             folded mod p
 //
-// Every fp32 sum is an exact integer below 2^24, so the result is the exact
-// residue: the same function as the integer-pipe form, bit for bit after
-// canonicalisation.  A group's threads meet at one named barrier per round
-// (A written, D of the previous round read) and wait on the group's
-// mbarrier for the tensor cores; every wait is bounded.
+// The 22 partial rounds (Alg. 1, MDSPartial) run in their unrolled form
+// (ChainParams): the dot products U_q with the partial rounds' input and the
+// deferred cell updates W s are contractions of round 3's S-box bytes and of
+// the 22 partial S-box outputs; only the chain c_q -> s_q = S(c_q + k_q) ->
+// c_(q+1) = U_q + sum_(r<=q) beta[q][r] s_r runs on the integer pipes, one
+// thread per state.
+//
+// Every fp32 sum is an exact integer below 2^24 (times 2^-24), so each result
+// is the exact residue: the same function as the integer-pipe form, bit for
+// bit after canonicalisation.  A group's threads meet at one named barrier
+// per contraction (operands written, the previous accumulators read) and
+// wait on the group's mbarrier for the tensor cores; every wait is bounded.
 #pragma once
+#include <cstddef>
+
 #include "poseidon.cuh"
 
 namespace pg12 {
 namespace dev {
 
-constexpr int kTcGroup = 128;                 // states (threads) per group
-constexpr int kTcAChunk = 128;                // bytes of one 8 x 8 fp16 core matrix
-constexpr int kTcAChunks = kTcK / 8;           // core-matrix columns of A (12)
+constexpr int kTcGroup = 128;                   // states (threads) per group
+constexpr int kTcAChunk = 128;                  // bytes of one 8 x 8 fp16 core matrix
+constexpr int kTcAChunks = kTcK / 8;            // core-matrix columns of A (12 input words)
 constexpr int kTcABytes = kTcGroup * kTcK * 2;  // A operand of a group: 24 KiB
-constexpr int kTcSlotBytes = kTcGroup * kT * 8;
-constexpr int kTcDCols = kTcN;                // columns of one group's D (96, a multiple of 32)
-// tensor-memory columns one CTA of `groups` groups allocates: a power of two
-// (at least 32) that holds every group's D
-constexpr int tc_tmem_alloc(int groups) {
-    return groups * kTcDCols <= 128 ? 128 : groups * kTcDCols <= 256 ? 256 : 512;
+constexpr int kTcRegion = 128;                  // tensor-memory columns of one group
+constexpr int kTcUStore = kTcN;                 // columns 96..119 of a region hold U_0 .. U_11
+// tensor-memory columns one CTA of `groups` groups allocates (a power of two)
+constexpr int tc_tmem_alloc(int groups) { return groups <= 1 ? 128 : groups <= 2 ? 256 : 512; }
+// instruction descriptor: fp16 A and B, fp32 D, both K-major, M = 128, N = n
+__host__ __device__ constexpr uint32_t tc_idesc(int n) {
+    return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kTcGroup >> 4) << 24);
 }
-// instruction descriptor: fp16 A and B, fp32 D, both K-major, N = 96, M = 128
-constexpr uint32_t kTcIdesc = (1u << 4) | ((uint32_t)(kTcN >> 3) << 17) | ((uint32_t)(kTcGroup >> 4) << 24);
 // a wait that has not seen the tensor cores finish after this many SM clocks gives up
 constexpr long long kTcWaitClocks = 4ll << 30;
 
-__device__ __align__(16) TcTables g_tc;  // uploaded with the other constant tables
+// byte offsets of the tables inside TcTables (and inside its shared-memory copy)
+constexpr uint32_t kTabM = offsetof(TcTables, m), kTabPre = offsetof(TcTables, pre);
+constexpr uint32_t kTabBBias = offsetof(TcTables, b_bias), kTabABias = offsetof(TcTables, a_bias);
+constexpr uint32_t kTabZcap = offsetof(TcTables, a_zcap);
+constexpr uint32_t kTabVpa = offsetof(TcTables, vpa), kTabVpb = offsetof(TcTables, vpb);
+constexpr uint32_t kTabW1 = offsetof(TcTables, w1), kTabW2 = offsetof(TcTables, w2);
+constexpr size_t kTabCore = offsetof(TcTables, vpa);  // what kernels without the chain copy
+static_assert(kTabVpa % 128 == 0 && kTabVpb % 128 == 0 && kTabW1 % 128 == 0 && kTabW2 % 128 == 0 &&
+                  kTabBBias % 128 == 0 && kTabZcap % 128 == 0,
+              "tables are 128-byte aligned");
+
+__device__ __align__(16) TcTables g_tc;     // uploaded with the other constant tables
+__constant__ uint64_t c_beta[kRP][kRP];     // ChainParams::beta
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -53,10 +71,10 @@ __device__ __forceinline__ uint64_t tc_desc(uint32_t addr, uint32_t lbo, uint32_
            ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
 
-__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t accumulate) {
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
     asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
-                 "l"(a), "l"(b), "r"(kTcIdesc), "r"(accumulate)
+                 "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
                  : "memory");
 }
 
@@ -99,7 +117,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity) {
     }
 }
 
-// 16 consecutive fp32 columns of this thread's TMEM lane.
+// Consecutive 32-bit columns of this thread's tensor-memory lane.
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
                  : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
@@ -107,38 +125,58 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
                  : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ uint64_t tmem_ld_word(uint32_t taddr) {
+    uint32_t lo, hi;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];" : "=r"(lo), "=r"(hi) : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    return ((uint64_t)hi << 32) | lo;
+}
+__device__ __forceinline__ void tmem_st_words(uint32_t taddr, uint64_t a, uint64_t b) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};" ::"r"(taddr), "r"(lo32(a)), "r"(hi32(a)),
+                 "r"(lo32(b)), "r"(hi32(b))
+                 : "memory");
+}
 
-// y = sum_b 2^(8b) w[b] mod p for eight column words w[b] < 2^31: two 56-bit
-// sums lo = sum_(b<4), hi = sum_(b>=4) (IMAD.WIDE with the running sum as
-// addend), V = lo + hi 2^32 < 2^88 = lo' + h 2^64 with lo' = lo + hi.lo 2^32
-// and h = hi.hi + carry, then the fold (2^64 = 2^32 - 1).
-__device__ __forceinline__ uint64_t tc_combine(const uint32_t *w) {
+// y = sum_b 2^(8b) w[b] + x mod p for eight column words w[b] < 2^31 and a
+// 64-bit x: two 56-bit sums lo = sum_(b<4), hi = sum_(b>=4) (IMAD.WIDE with
+// the running sum as addend), V = lo + hi 2^32 + x < 2^89 = lo' + h 2^64 with
+// lo' = lo + x + hi.lo 2^32 and h = hi.hi + carries, then the fold
+// (2^64 = 2^32 - 1).
+__device__ __forceinline__ uint64_t tc_combine(const uint32_t *w, uint64_t x = 0) {
     uint64_t lo = madw(w[1], 1u << 8, (uint64_t)w[0]);
     lo = madw(w[2], 1u << 16, lo);
     lo = madw(w[3], 1u << 24, lo);
     uint64_t hi = madw(w[5], 1u << 8, (uint64_t)w[4]);
     hi = madw(w[6], 1u << 16, hi);
     hi = madw(w[7], 1u << 24, hi);
-    uint32_t l1, h;
-    asm("add.cc.u32 %0, %2, %3;\n\t"
-        "addc.u32 %1, %4, 0;"
-        : "=r"(l1), "=r"(h)
-        : "r"(hi32(lo)), "r"(lo32(hi)), "r"(hi32(hi)));
-    return fold(((uint64_t)l1 << 32) | lo32(lo), (uint64_t)h, 0);
+    uint32_t l0, l1, h;
+    asm("add.cc.u32 %0, %3, %5;\n\t"
+        "addc.cc.u32 %1, %4, %6;\n\t"
+        "addc.u32 %2, %8, 0;\n\t"
+        "add.cc.u32 %1, %1, %7;\n\t"
+        "addc.u32 %2, %2, 0;"
+        : "=r"(l0), "=r"(l1), "=r"(h)
+        : "r"(lo32(lo)), "r"(hi32(lo)), "r"(lo32(x)), "r"(hi32(x)), "r"(lo32(hi)), "r"(hi32(hi)));
+    return fold(((uint64_t)l1 << 32) | l0, (uint64_t)h, 0);
 }
 
 // One group's share of the CTA's shared memory and tensor memory.
 struct TcGroup {
     uint8_t *a;           // A operand, kTcABytes
-    uint64_t *slot;       // states: cell i of thread t at slot[i * kTcGroup + t]
     uint64_t *mbar;       // tensor-core completion barrier
-    uint32_t tmem;        // D: lanes 0..127, kTcDCols columns
+    uint32_t tmem;        // the group's kTcRegion columns, lanes 0..127
     uint32_t phase;       // parity of the mbarrier's next completion
     int bar;              // named barrier of the group's 128 threads
     int t;                // thread index within the group
     uint32_t failed;      // this thread saw a tensor-core wait run out
     volatile uint32_t *bcast;  // one word through which thread 0 hands the group a value
-    uint32_t a_addr, b_addr, bias_addr, zcap_addr;  // shared addresses for the descriptors
+    uint32_t a_addr, tab;      // shared addresses of A and of the tables
 };
 
 // Row t's chunk j of A (K columns 8j..8j+7) <- the 8 bytes of y as fp16 subnormals.
@@ -152,26 +190,30 @@ __device__ __forceinline__ void tc_put(const TcGroup &G, int j, uint64_t y) {
     *reinterpret_cast<uint4 *>(G.a + ((G.t >> 3) * kTcAChunks + j) * kTcAChunk + (G.t & 7) * 16) = v;
 }
 
-
-// Dense layer of round r (matrix m: 0 = M, 1 = transition) on the states
-// whose S-box outputs are in A; writes rows 0..rows-1 of the result to the
-// slots.  z: round 0 of states whose capacity entered as zero (A holds
-// cells 0..7; cells 8..11 come from the constant zcap pattern).  Returns
-// false, in every thread of the group, once a wait of the group has run out.
-__device__ __forceinline__ bool tc_dense(TcGroup &G, int m, bool z, int rows) {
+// One contraction into the group's D (columns 0 .. n-1): the group meets
+// (its A stores visible to the tensor cores, its earlier tensor-memory
+// accesses done), thread 0 issues the bias block (when `bias`: D starts at
+// the bias; else D accumulates) and kblocks K = 16 blocks of A (cells 8..11
+// from the zero-capacity block when z) against the table at byte offset
+// b_off with b_chunks input words per row group, and commits; every thread
+// waits.  Returns false, in every thread of the group, once a wait of the
+// group has run out.
+__device__ __forceinline__ bool tc_contract(TcGroup &G, uint32_t b_off, uint32_t b_chunks, int n, int kblocks,
+                                            bool bias, bool z) {
     fence_async_smem();   // this thread's A stores -> the tensor cores' proxy
-    tc_fence_before();    // its tensor-memory reads of the previous round are complete
+    tc_fence_before();    // its tensor-memory accesses are complete
     if (group_sync_or(G.bar, G.failed)) return false;
     if (G.t == 0) {
         tc_fence_after();
-        const uint32_t bm = G.b_addr + (uint32_t)m * (uint32_t)sizeof(TcTables::b[0]);
-        constexpr uint32_t sbo_b = kTcKC * kTcAChunk, sbo_a = kTcAChunks * kTcAChunk;
-        tc_mma(G.tmem, tc_desc(G.bias_addr, kTcAChunk, 0), tc_desc(bm + 12 * kTcAChunk, kTcAChunk, sbo_b), 0);
-#pragma unroll
-        for (int kb = 0; kb < 6; ++kb) {
-            const uint64_t a = (z && kb >= 4) ? tc_desc(G.zcap_addr + (kb - 4) * 2 * kTcAChunk, kTcAChunk, 0)
+        const uint32_t idesc = tc_idesc(n);
+        const uint32_t sbo_b = b_chunks * kTcAChunk, sbo_a = kTcAChunks * kTcAChunk;
+        if (bias)
+            tc_mma(G.tmem, tc_desc(G.tab + kTabABias, kTcAChunk, 0), tc_desc(G.tab + kTabBBias, kTcAChunk, 0), idesc,
+                   0);
+        for (int kb = 0; kb < kblocks; ++kb) {
+            const uint64_t a = (z && kb >= 4) ? tc_desc(G.tab + kTabZcap + (kb - 4) * 2 * kTcAChunk, kTcAChunk, 0)
                                               : tc_desc(G.a_addr + kb * 2 * kTcAChunk, kTcAChunk, sbo_a);
-            tc_mma(G.tmem, a, tc_desc(bm + kb * 2 * kTcAChunk, kTcAChunk, sbo_b), 1);
+            tc_mma(G.tmem, a, tc_desc(G.tab + b_off + kb * 2 * kTcAChunk, kTcAChunk, sbo_b), idesc, 1);
         }
         tc_commit(G.mbar);
     }
@@ -179,75 +221,165 @@ __device__ __forceinline__ bool tc_dense(TcGroup &G, int m, bool z, int rows) {
     G.phase ^= 1u;
     if (!ok) G.failed = 1;
     tc_fence_after();
+    return true;
+}
+
+// Dense layer of a full round (table at m_off) on the S-box outputs in A;
+// rows 0..rows-1 of the result go to x.  z: round 0 of states whose
+// capacity entered as zero (A holds cells 0..7; cells 8..11 come from the
+// constant zcap block).
+__device__ __forceinline__ bool tc_dense(TcGroup &G, uint32_t m_off, bool z, int rows, uint64_t (&x)[kT]) {
+    if (!tc_contract(G, m_off, kTcAChunks, kTcN, 6, true, z)) return false;
     const uint32_t lane_base = G.tmem + ((uint32_t)(G.t & ~31) << 16);
-    uint64_t *slot = G.slot + G.t;
-#pragma unroll 1
-    for (int i = 0; i < rows; i += 2) {
-        uint32_t w[16];
-        tmem_ld16(lane_base + 8 * i, w);
-        slot[i * kTcGroup] = tc_combine(w);
-        slot[(i + 1) * kTcGroup] = tc_combine(w + 8);
+#pragma unroll
+    for (int i = 0; i < kT; i += 2) {
+        if (i < rows) {
+            uint32_t w[16];
+            tmem_ld16(lane_base + 8 * i, w);
+            x[i] = tc_combine(w);
+            x[i + 1] = tc_combine(w + 8);
+        }
     }
     return true;
 }
 
-// Code shape of the tensor-core path (measured on the 2^22 x 8 tree, 4
-// groups): S-boxes four cells per loop iteration and the partial rounds'
-// eleven cells unrolled in registers, 10.25 ms; two cells per iteration and
-// the cells walked in the slots (the integer-pipe kernels' shape), 10.67 ms.
-#ifndef PG12_TC_SBOX_CELLS
-#define PG12_TC_SBOX_CELLS 4  // 1, 2 or 4 (divides 8 and 12)
-#endif
-#ifndef PG12_TC_PARTIAL_LOOP
-#define PG12_TC_PARTIAL_LOOP 0
-#endif
+// The 22 partial rounds in their unrolled form, after round 3's dense layer
+// (A still holds round 3's S-box bytes y3, x holds x^(0) = P y3).
+__device__ __forceinline__ bool tc_partial(TcGroup &G, uint64_t (&x)[kT]) {
+    const uint32_t lane_base = G.tmem + ((uint32_t)(G.t & ~31) << 16);
+    // U_0 .. U_11, kept as words in columns 96..119 of the group's region
+    if (!tc_contract(G, kTabVpa, kTcAChunks, kTcN, 6, true, false)) return false;
+#pragma unroll
+    for (int i = 0; i < kT; i += 2) {
+        uint32_t w[16];
+        tmem_ld16(lane_base + 8 * i, w);
+        tmem_st_words(lane_base + kTcUStore + 2 * i, tc_combine(w), tc_combine(w + 8));
+    }
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    // U_12 .. U_21 as column sums in D columns 0..79
+    if (!tc_contract(G, kTabVpb, kTcAChunks, kTcUb * 8, 6, true, false)) return false;
+    // the chain; s_q in A (free now) as plain words, sst[q * 128]
+    uint64_t *sst = reinterpret_cast<uint64_t *>(G.a) + G.t;
+    uint64_t c = x[0];
+#pragma unroll 1
+    for (int q = 0;; ++q) {
+        const uint64_t s = sbox(add_canon(c, c_dev.part_rc[q]));
+        sst[q * kTcGroup] = s;
+        if (q == kRP - 1) break;
+        uint64_t u;
+        if (q < kT) {
+            u = tmem_ld_word(lane_base + kTcUStore + 2 * q);
+        } else {
+            uint32_t w[8];
+            tmem_ld8(lane_base + 8 * (q - kT), w);
+            u = tc_combine(w);
+        }
+        Acc A;
+        acc_init(A, u);
+#pragma unroll 1
+        for (int r = 0; r <= q; ++r) acc_mac(A, sst[r * kTcGroup], c_beta[q][r]);
+        c = acc_reduce(A);
+    }
+    uint64_t u21;
+    {
+        uint32_t w[8];
+        tmem_ld8(lane_base + 8 * (kRP - 1 - kT), w);
+        u21 = tc_combine(w);
+    }
+    // the deferred updates W s: s_0 .. s_11, then s_12 .. s_21, into one sum
+    uint64_t sv[kRP];
+#pragma unroll
+    for (int r = 0; r < kRP; ++r) sv[r] = sst[r * kTcGroup];
+    group_sync(G.bar);  // every thread has its s before A's rows are overwritten
+#pragma unroll
+    for (int j = 0; j < kT; ++j) tc_put(G, j, sv[j]);
+    if (!tc_contract(G, kTabW1, kTcAChunks, kTcN, 6, true, false)) return false;
+#pragma unroll
+    for (int j = 0; j < kTcW2; ++j) tc_put(G, j, sv[kT + j]);
+    if (!tc_contract(G, kTabW2, kTcW2, kTcN, kTcW2 / 2, false, false)) return false;
+    // cell 0 = c_22 = U_21 + (W s)_0, cell i = x_i^(0) + (W s)_i
+#pragma unroll
+    for (int i = 0; i < kT; i += 2) {
+        uint32_t w[16];
+        tmem_ld16(lane_base + 8 * i, w);
+        x[i] = tc_combine(w, i == 0 ? u21 : x[i]);
+        x[i + 1] = tc_combine(w + 8, x[i + 1]);
+    }
+    return true;
+}
 
-// The permutation on the group's slots (weak words in, weak words out),
-// with the same zcap / digest shortcuts as permute_slot.
-__device__ __forceinline__ bool tc_permute(TcGroup &G, bool zcap, bool digest) {
-    uint64_t *slot = G.slot + G.t;
+// The 22 partial rounds on the integer pipes, state in registers (the
+// MDSPartial form of Alg. 1: 12 products for cell 0, 11 multiply-adds).
+__device__ __forceinline__ void partial_regs(uint64_t (&x)[kT]) {
+#pragma unroll 1
+    for (int q = 0; q < kRP; ++q) {
+        const uint64_t x0 = sbox(add_canon(x[0], c_dev.part_rc[q]));
+        Acc A;
+        acc_zero(A);
+        acc_mac(A, x0, c_dev.part_v[q][0]);
+#pragma unroll
+        for (int j = 1; j < kT; ++j) acc_mac(A, x[j], c_dev.part_v[q][j]);
+#pragma unroll
+        for (int i = 1; i < kT; ++i) x[i] = mul_add(c_dev.part_w[q][i], x0, x[i]);
+        x[0] = acc_reduce(A);
+    }
+}
+
+// The permutation on x, the thread's state in registers (weak words in,
+// weak words out), with the same zcap / digest shortcuts as permute_slot.
+// Each round's twelve S-boxes and twelve output folds are unrolled (the
+// state never leaves registers).  CHAIN: the partial rounds in their
+// unrolled form on the tensor cores (tc_partial); else on the integer pipes
+// (partial_regs).
+template <bool CHAIN>
+__device__ __forceinline__ bool tc_permute(TcGroup &G, uint64_t (&x)[kT], bool zcap, bool digest) {
 #pragma unroll 1
     for (int r = 0; r < kRF; ++r) {
         const bool z = zcap && r == 0;
-        const int cells = z ? kRate : kT;
-#pragma unroll 1
-        for (int j = 0; j < cells; j += PG12_TC_SBOX_CELLS) {
-            uint64_t a[PG12_TC_SBOX_CELLS];
 #pragma unroll
-            for (int k = 0; k < PG12_TC_SBOX_CELLS; ++k) a[k] = add_canon(slot[(j + k) * kTcGroup], c_dev.full_rc[r][j + k]);
+        for (int j = 0; j < kRate; ++j) tc_put(G, j, sbox(add_canon(x[j], c_dev.full_rc[r][j])));
+        if (!z) {
 #pragma unroll
-            for (int k = 0; k < PG12_TC_SBOX_CELLS; ++k) tc_put(G, j + k, sbox(a[k]));
+            for (int j = kRate; j < kT; ++j) tc_put(G, j, sbox(add_canon(x[j], c_dev.full_rc[r][j])));
         }
-        if (!tc_dense(G, r == kRF / 2 - 1 ? 1 : 0, z, digest && r == kRF - 1 ? kDigest : kT)) return false;
-        if (r == kRF / 2 - 1) partial_phase<kTcGroup, PG12_TC_PARTIAL_LOOP>(slot);
+        const bool mid = r == kRF / 2 - 1;
+        if (!tc_dense(G, mid ? kTabPre : kTabM, z, digest && r == kRF - 1 ? kDigest : kT, x)) return false;
+        if (mid) {
+            if (CHAIN) {
+                if (!tc_partial(G, x)) return false;
+            } else {
+                partial_regs(x);
+            }
+        }
     }
     return true;
 }
 
-// Shared-memory layout of a CTA of GROUPS groups: the tables, then each
-// group's A operand, then each group's state slots, then the barriers.
-template <int GROUPS>
+// Shared-memory layout of a CTA of GROUPS groups: the tables (all of them
+// with CHAIN, else the full rounds' part), then each group's A operand, then
+// the barriers.
+template <int GROUPS, bool CHAIN>
 struct TcLayout {
-    static_assert(GROUPS * kTcDCols <= 512, "the groups' accumulators exceed tensor memory");
+    static_assert(GROUPS * kTcRegion <= 512, "the groups' tensor memory exceeds the SM's");
     static constexpr int kTmemCols = tc_tmem_alloc(GROUPS);
+    static constexpr size_t kTableBytes = CHAIN ? sizeof(TcTables) : kTabCore;
     static constexpr size_t kTables = 0;
-    static constexpr size_t kA = (sizeof(TcTables) + 127) & ~(size_t)127;
-    static constexpr size_t kSlot = kA + (size_t)GROUPS * kTcABytes;
-    static constexpr size_t kBar = kSlot + (size_t)GROUPS * kTcSlotBytes;
+    static constexpr size_t kA = (kTableBytes + 127) & ~(size_t)127;
+    static constexpr size_t kBar = kA + (size_t)GROUPS * kTcABytes;
     static constexpr size_t kBcast = kBar + 8 * GROUPS + 16;
     static constexpr size_t kBytes = kBcast + 4 * GROUPS;
 };
 
-__device__ int g_tc_fault;  // set when a tensor-core wait ran out (read by pg_device_flags)
+__device__ int g_tc_fault;  // set when a tensor-core wait ran out (read by pg_device_faults)
 
 // Prologue of a tensor-core kernel: tables into shared memory, the groups'
 // barriers, one tensor-memory allocation for all groups.
-template <int GROUPS>
+template <int GROUPS, bool CHAIN>
 __device__ __forceinline__ TcGroup tc_setup(uint8_t *sm) {
-    using L = TcLayout<GROUPS>;
+    using L = TcLayout<GROUPS, CHAIN>;
     const uint4 *src = reinterpret_cast<const uint4 *>(&g_tc);
     uint4 *dst = reinterpret_cast<uint4 *>(sm + L::kTables);
-    for (unsigned i = threadIdx.x; i < sizeof(TcTables) / 16; i += blockDim.x) dst[i] = __ldg(src + i);
+    for (unsigned i = threadIdx.x; i < L::kTableBytes / 16; i += blockDim.x) dst[i] = __ldg(src + i);
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + L::kBar);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + GROUPS);
     if (threadIdx.x == 0) {
@@ -268,17 +400,13 @@ __device__ __forceinline__ TcGroup tc_setup(uint8_t *sm) {
     G.t = threadIdx.x % kTcGroup;
     G.failed = 0;
     G.a = sm + L::kA + (size_t)g * kTcABytes;
-    G.slot = reinterpret_cast<uint64_t *>(sm + L::kSlot + (size_t)g * kTcSlotBytes);
     G.mbar = bars + g;
-    G.tmem = *tslot + (uint32_t)(g * kTcDCols);
+    G.tmem = *tslot + (uint32_t)(g * kTcRegion);
     G.phase = 0;
     G.bar = 1 + g;
     G.bcast = reinterpret_cast<volatile uint32_t *>(sm + L::kBcast) + g;
-    const TcTables *T = reinterpret_cast<const TcTables *>(sm + L::kTables);
     G.a_addr = smem_addr(G.a);
-    G.b_addr = smem_addr(T->b[0]);
-    G.bias_addr = smem_addr(T->a_bias);
-    G.zcap_addr = smem_addr(T->a_zcap);
+    G.tab = smem_addr(sm + L::kTables);
     return G;
 }
 
@@ -296,9 +424,9 @@ __device__ __forceinline__ uint32_t group_fetch_add(TcGroup &G, uint32_t *counte
 // Epilogue: every group is done with tensor memory; the allocating warp
 // frees it.  A group whose wait ran out records the fault and gives its
 // last contraction one more bounded wait before the memory is freed.
-template <int GROUPS>
+template <int GROUPS, bool CHAIN>
 __device__ __forceinline__ void tc_teardown(uint8_t *sm, TcGroup &G) {
-    using L = TcLayout<GROUPS>;
+    using L = TcLayout<GROUPS, CHAIN>;
     if (G.failed) {
         atomicExch(&g_tc_fault, 1);
         if (G.t == 0) mbar_wait(G.mbar, G.phase ^ 1u);

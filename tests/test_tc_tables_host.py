@@ -1,27 +1,33 @@
-"""CPU pins of the tensor-core form of the full rounds' dense layers.
+"""CPU pins of the tensor-core forms: the digit tables and the unrolled partial rounds.
 
-The library's tensor-core kernels compute y = M x (Alg. 1, MDS) for 128
-states at a time as an fp32 contraction of byte limbs (the digit tables of
-pg_tc_tables_export).  These tests take the exported tables and redo, with
-Python integers, exactly what the tensor cores and the combination step
-compute -- bytes of x times the decoded fp16 digits, plus the bias row, as
-fp32 bit patterns, then sum_b 2^(8b) bits mod p -- and require the result to
-equal the plain matrix-vector product mod p, for both parameter sets and
-both matrices (M, and the transition matrix of round 3), on random and
-extreme inputs.  They also check every bound the exactness argument needs:
-digits in [-128, 127], every fp32 sum an integer in [2^23, 2^24) for any
-input bytes, and the bias offsets cancelling mod p.
+The tensor-core kernels compute each dense contraction (the full rounds'
+M y, Alg. 1; the partial rounds' dot products U = (V' P) y3 and deferred
+updates W s, their unrolled form) for 128 states at a time as an fp32
+contraction of byte limbs (the digit tables of pg_tc_tables_export).  These
+tests take the exported tables and redo, with Python integers, exactly what
+the tensor cores and the combination step compute -- bytes of the operand
+words times the decoded fp16 digits, plus the bias block, as fp32 bit
+patterns, then sum_b 2^(8b) bits mod p -- and require the plain
+matrix-vector products mod p, for both parameter sets, on random and extreme
+inputs.  They check every bound the exactness argument needs (digits in
+[-128, 127]; every fp32 sum an integer in [2^23, 2^24) for any input bytes,
+including the final updates that accumulate two tables) and that the bias
+offsets cancel mod p.  And they evaluate the whole permutation in the
+unrolled form (pg_params_export_chain) against the oracle's plain Alg. 1.
 """
 import numpy as np
 import pytest
 
+import oracle
 import pg_synth
 
 pg = pytest.importorskip("paper_2506_09505_gb300")
 
 P = 0xFFFFFFFF00000001
 T = 12
-KC = 14
+RP = 22
+TABLES = [("m", 12, 12), ("pre", 12, 12), ("b_bias", None, None), ("a_bias", None, None), ("a_zcap", None, None),
+          ("vpa", 12, 12), ("vpb", 10, 12), ("w1", 12, 12), ("w2", 12, 10)]
 
 
 def half_to_float(h: int) -> float:
@@ -31,100 +37,162 @@ def half_to_float(h: int) -> float:
 def tables(params=None):
     pg.load(build_if_missing=True)
     pg.params_select(params)
-    raw = pg.tc_tables_export()
-    h = np.frombuffer(raw, dtype=np.uint16)
-    nb = 96 * KC * 8
-    b = h[:2 * nb].reshape(2, nb)
-    a_bias = h[2 * nb:2 * nb + 128]
-    a_zcap = h[2 * nb + 128:2 * nb + 128 + 256]
-    return b, a_bias, a_zcap
+    h = np.frombuffer(pg.tc_tables_export(), dtype=np.uint16)
+    out, off = {}, 0
+    for name, n, k in TABLES:
+        # a table: 8n rows x 8k columns; the bias blocks two core matrices, zcap four
+        size = (8 * n) * (8 * k) if n else (256 if name == "a_zcap" else 128)
+        out[name] = h[off:off + size]
+        off += size
+    assert off == h.size
+    return out
 
 
-def b_entry(bt, n, k):
-    """B operand value at output column n, K column k (K-major core matrices)."""
-    c, a = divmod(k, 8)
-    return half_to_float(int(bt[(n // 8 * KC + c) * 64 + (n % 8) * 8 + a]))
+def decode(tab, n, k):
+    """digits[i][b][j][a] of an n x k table (K-major core matrices, k chunks per row group)."""
+    dig = np.zeros((n, 8, k, 8), dtype=np.int64)
+    for row in range(8 * n):
+        i, b = divmod(row, 8)
+        for j in range(k):
+            base = (row // 8 * k + j) * 64 + (row % 8) * 8
+            for a in range(8):
+                v = half_to_float(int(tab[base + a]))
+                assert v == int(v)
+                dig[i, b, j, a] = int(v)
+    return dig
 
 
-def decode(bt):
-    """digits[i][b][j][a] (integers) and bias value per output column."""
-    dig = np.zeros((T, 8, T, 8), dtype=np.int64)
-    bias = np.zeros(96)
-    for n in range(96):
-        i, bb = divmod(n, 8)
-        for k in range(96):
-            j, a = divmod(k, 8)
-            v = b_entry(bt, n, k)
-            assert v == int(v)
-            dig[i, bb, j, a] = int(v)
-        bias[n] = b_entry(bt, n, 96)
-        for k in range(97, 112):
-            assert b_entry(bt, n, k) == 0.0
-    return dig, bias
+def bias_magic(t):
+    """magic_b (integers, scaled by 2^24) from the bias blocks."""
+    a = half_to_float(int(t["a_bias"][0]))
+    assert a == 2.0 ** -13
+    for r in range(8):
+        for k in range(16):
+            assert int(t["a_bias"][(k // 8) * 64 + r * 8 + k % 8]) == (0x0800 if k == 0 else 0)
+    mags = []
+    for b in range(8):
+        for k in range(16):
+            if k:
+                assert int(t["b_bias"][(k // 8) * 64 + b * 8 + k % 8]) == 0
+        mags.append(int(round(half_to_float(int(t["b_bias"][b * 8])) * a * 2 ** 24)))
+    return mags
 
 
-def dense_via_tables(dig, bias_prod, x):
-    """What the kernels compute for one state x (12 weak words)."""
-    xb = np.array([[(int(v) >> (8 * a)) & 0xFF for a in range(8)] for v in x], dtype=np.int64)
+def contract(digs, magic, words_list):
+    """What the kernels compute: sum over the tables (one accumulator) of bytes x digits, plus the bias."""
+    n = digs[0].shape[0]
     out = []
-    for i in range(T):
+    for i in range(n):
         acc = 0
         for bb in range(8):
-            z = int((dig[i, bb] * xb).sum())
-            magic = int(round(bias_prod[8 * i + bb] * 2**24))
-            v = magic + z
+            z = 0
+            for dig, words in zip(digs, words_list):
+                xb = np.array([[(int(v) >> (8 * a)) & 0xFF for a in range(8)] for v in words], dtype=np.int64)
+                z += int((dig[i, bb] * xb).sum())
+            v = magic[bb] + z
             assert (1 << 23) <= v < (1 << 24), "fp32 sum outside [2^23, 2^24): not exact"
-            bits = 0x3F000000 + (v - (1 << 23))  # fp32 bits of v * 2^-24 in [0.5, 1)
-            acc += bits << (8 * bb)
+            acc += (0x3F000000 + (v - (1 << 23))) << (8 * bb)  # fp32 bits of v * 2^-24
         out.append(acc % P)
     return out
 
 
-def plain_dense(m, x):
-    return [sum(int(m[i][j]) * (int(x[j]) % P) for j in range(T)) % P for i in range(T)]
+def plain(mat, words):
+    return [sum(int(mat[i][j]) * (int(words[j]) % P) for j in range(len(words))) % P for i in range(len(mat))]
+
+
+def worst_window(digs, magic):
+    """Every column's extreme sums over all byte inputs stay in the exact window."""
+    for i in range(digs[0].shape[0]):
+        for bb in range(8):
+            pos = sum(int(d[i, bb][d[i, bb] > 0].sum()) for d in digs)
+            neg = sum(int(-d[i, bb][d[i, bb] < 0].sum()) for d in digs)
+            assert magic[bb] - 255 * neg >= 1 << 23 and magic[bb] + 255 * pos < 1 << 24
+
+
+def _inputs(k, seed):
+    xs = [pg_synth.words(seed + t, k, bound=None) for t in range(4)]
+    xs.append(np.full(k, (1 << 64) - 1, dtype=np.uint64))   # every byte 255
+    xs.append(np.zeros(k, dtype=np.uint64))
+    xs.append(np.full(k, P - 1, dtype=np.uint64))
+    return xs
 
 
 @pytest.mark.parametrize("params", [None, "pg12_small"])
-def test_digit_tables_reproduce_the_dense_layers(params):
-    b, a_bias, a_zcap = tables(params)
+def test_digit_tables_reproduce_every_contraction(params):
+    t = tables(params)
     opt = pg.params_export_optimized()
-    a_scale = half_to_float(int(a_bias[0]))
-    assert a_scale == 2.0**-13
-    # the bias A operand is 2^-13 at column 0 of every row of both core matrices, else 0
-    for r in range(8):
-        for k in range(16):
-            want = 0x0800 if k == 0 else 0
-            assert int(a_bias[(k // 8) * 64 + r * 8 + k % 8]) == want
-    xs = [pg_synth.words(0x7C00 + k, T, bound=None) for k in range(6)]
-    xs.append(np.full(T, (1 << 64) - 1, dtype=np.uint64))   # every byte 255
-    xs.append(np.zeros(T, dtype=np.uint64))
-    xs.append(np.full(T, P - 1, dtype=np.uint64))
-    for m, mat in ((0, opt["mds"]), (1, opt["pre"])):
-        dig, bias = decode(b[m])
+    vp, beta, w = pg.params_export_chain()
+    magic = bias_magic(t)
+    cases = [("m", opt["mds"], 12), ("pre", opt["pre"], 12), ("vpa", vp[:12], 12), ("vpb", vp[12:], 12)]
+    for name, mat, k in cases:
+        dig = decode(t[name], len(mat), k)
         assert dig.min() >= -128 and dig.max() <= 127
-        # worst-case |Z| over all byte inputs stays inside the exact window
-        zmax = int(np.abs(dig).sum(axis=(2, 3)).max()) * 255
-        magic = bias * a_scale * 2**24
-        assert (magic - zmax >= 2**23).all() and (magic + zmax < 2**24).all()
-        for x in xs:
-            assert dense_via_tables(dig, bias * a_scale, x) == plain_dense(mat, x)
+        worst_window([dig], magic)
+        for x in _inputs(k, 0x7C00):
+            assert contract([dig], magic, [x]) == plain(mat, x), name
+    # the final updates: two tables into one accumulator
+    d1, d2 = decode(t["w1"], 12, 12), decode(t["w2"], 12, 10)
+    worst_window([d1, d2], magic)
+    for s in _inputs(22, 0x7D00):
+        assert contract([d1, d2], magic, [s[:12], s[12:]]) == plain(w, s)
     pg.params_select(None)
 
 
 def test_bias_offsets_cancel_mod_p():
-    b, a_bias, _ = tables(None)
-    _, bias = decode(b[0])
-    magic = [int(round(v * 2.0**-13 * 2**24)) for v in bias[:8]]
+    magic = bias_magic(tables(None))
     assert sum((0x3E800000 + mg) << (8 * bb) for bb, mg in enumerate(magic)) % P == 0
-    for i in range(1, T):   # every output row uses the same eight biases
-        assert list(bias[8 * i:8 * i + 8]) == list(bias[:8])
 
 
 def test_zero_capacity_pattern_is_the_constant_sbox_outputs():
-    _, _, a_zcap = tables(None)
+    t = tables(None)
     opt = pg.params_export_optimized()
     for j in range(8, 12):
         c7 = pow(int(opt["full_rc"][0][j]) % P, 7, P)
         for r in range(8):
-            got = sum(int(a_zcap[(j - 8) * 64 + r * 8 + a]) << (8 * a) for a in range(8))
+            got = sum(int(t["a_zcap"][(j - 8) * 64 + r * 8 + a]) << (8 * a) for a in range(8))
             assert got == c7
+
+
+def _chain_permute(x, op, vp, beta, w):
+    """Alg. 1 with the partial rounds in their unrolled form (Python integers)."""
+    x = [int(v) % P for v in x]
+    fr, M, pre = op["full_rc"], op["mds"], op["pre"]
+
+    def sbox_layer(x, r):
+        return [pow((x[i] + int(fr[r, i])) % P, 7, P) for i in range(12)]
+
+    def dense(mat, y):
+        return [sum(int(mat[i, j]) * y[j] for j in range(12)) % P for i in range(12)]
+    for r in range(3):
+        x = dense(M, sbox_layer(x, r))
+    y3 = sbox_layer(x, 3)
+    x0 = dense(pre, y3)
+    u = [sum(int(vp[q, j]) * y3[j] for j in range(12)) % P for q in range(RP)]
+    c, s = x0[0], []
+    for q in range(RP):
+        s.append(pow((c + int(op["part_rc"][q])) % P, 7, P))
+        if q < RP - 1:
+            c = (u[q] + sum(int(beta[q, r]) * s[r] for r in range(q + 1))) % P
+    ws = [sum(int(w[i, r]) * s[r] for r in range(RP)) % P for i in range(12)]
+    x = [(u[RP - 1] + ws[0]) % P] + [(x0[i] + ws[i]) % P for i in range(1, 12)]
+    for r in range(4, 8):
+        x = dense(M, sbox_layer(x, r))
+    return x
+
+
+@pytest.mark.parametrize("params", [None, "pg12_small"])
+def test_unrolled_partial_rounds_equal_the_plain_permutation(params):
+    pg.load(build_if_missing=True)
+    pg.params_select(params)
+    try:
+        op = pg.params_export_optimized()
+        vp, beta, w = pg.params_export_chain()
+        rc, mds = (oracle.params() if params is None else oracle.params_small())[:2]
+        st = pg_synth.matrix(0xCA1 + (params is not None), 24, 12)
+        st[0] = 0
+        st[1] = np.uint64((1 << 64) - 1)
+        want = oracle.permute(st, rc=rc, mds=mds)
+        for k in range(st.shape[0]):
+            assert _chain_permute(st[k], op, vp, beta, w) == [int(v) for v in want[k]]
+    finally:
+        pg.params_select(None)
