@@ -401,21 +401,21 @@ bool build_tc_tables(const OptParams &op, TcTables &tt) {
 
     ChainParams cp;
     derive_chain(op, cp);
-    static uint64_t m[kT * kT], pre[kT * kT], vpa[kT * kT], vpb[kTcUb * kT], w1[kT * kT], w2[kT * kTcW2];
+    static uint64_t m[kT * kT], pre[kT * kT], vpa[kTcUa * kT], vpb[kT * kT], bs[kT * kT], w1[kT * kT], w2[kT * kT];
     for (int i = 0; i < kT; ++i)
         for (int j = 0; j < kT; ++j) {
             m[i * kT + j] = op.mds[i][j] % kP;
             pre[i * kT + j] = op.pre[i][j] % kP;
-            vpa[i * kT + j] = cp.vp[i][j];
-            w1[i * kT + j] = cp.w[i][j];
+            if (i < kTcUa) vpa[i * kT + j] = cp.vp[i][j];
+            vpb[i * kT + j] = cp.vp[kTcUa + i][j];
+            const int q = kTcUa + i;  // bs: the first half's s_r in c_(q+1), q = 10 .. 20
+            bs[i * kT + j] = (q < kRP - 1 && j < kTcSplit) ? cp.beta[q][j] : 0;
+            w1[i * kT + j] = j < kTcSplit ? cp.w[i][j] : 0;
+            w2[i * kT + j] = j < kRP - kTcSplit ? cp.w[i][kTcSplit + j] : 0;
         }
-    for (int i = 0; i < kTcUb; ++i)
-        for (int j = 0; j < kT; ++j) vpb[i * kT + j] = cp.vp[kT + i][j];
-    for (int i = 0; i < kT; ++i)
-        for (int j = 0; j < kTcW2; ++j) w2[i * kTcW2 + j] = cp.w[i][kT + j];
     // every accumulation's worst sums: magic_b - 255 neg >= 2^23 and
-    // magic_b + 255 pos < 2^24 for each column; the final cells accumulate
-    // the two W tables into one sum
+    // magic_b + 255 pos < 2^24 for each column; the second half's chain values
+    // accumulate vpb and bs into one sum, the final cells w1 and w2
     bool ok = true;
     auto check = [&](const long *pos, const long *neg, int rows) {
         for (int r = 0; r < rows; ++r) {
@@ -435,18 +435,19 @@ bool build_tc_tables(const OptParams &op, TcTables &tt) {
     }
     {
         long pos[kTcN] = {}, neg[kTcN] = {};
-        digit_table(vpa, kT, kT, tt.vpa, pos, neg);
+        digit_table(vpa, kTcUa, kT, tt.vpa, pos, neg);
+        check(pos, neg, kTcUa * 8);
+    }
+    {
+        long pos[kTcN] = {}, neg[kTcN] = {};
+        digit_table(vpb, kT, kT, tt.vpb, pos, neg);
+        digit_table(bs, kT, kT, tt.bs, pos, neg);
         check(pos, neg, kTcN);
     }
     {
         long pos[kTcN] = {}, neg[kTcN] = {};
-        digit_table(vpb, kTcUb, kT, tt.vpb, pos, neg);
-        check(pos, neg, kTcUb * 8);
-    }
-    {
-        long pos[kTcN] = {}, neg[kTcN] = {};
         digit_table(w1, kT, kT, tt.w1, pos, neg);
-        digit_table(w2, kT, kTcW2, tt.w2, pos, neg);
+        digit_table(w2, kT, kT, tt.w2, pos, neg);
         check(pos, neg, kTcN);
     }
     for (int j = kRate; j < kT; ++j) {

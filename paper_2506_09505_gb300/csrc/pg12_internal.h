@@ -68,8 +68,12 @@ struct ChainParams {
 // (row group g, column chunk c) at halfs (g k + c) * 64.
 constexpr int kTcN = kT * 8;   // output columns (i, b) of a 12-row table
 constexpr int kTcK = kT * 8;   // K of a 12-word input
-constexpr int kTcUb = kRP - kT;  // rows of the second U table (U_12 .. U_21)
-constexpr int kTcW2 = kRP - kT;  // input words of the second W table (s_12 .. s_21)
+// The chain runs in two halves: s_0 .. s_10, then s_11 .. s_21; between them
+// the first half's contributions to the second half's chain values are one
+// contraction (the bs table).
+constexpr int kTcSplit = 11;       // S-box outputs of the first half
+constexpr int kTcUa = kTcSplit - 1;  // rows of the first U table (U_0 .. U_9)
+static_assert(kRP - kTcUa == kT && kRP - kTcSplit < kT, "each table has at most 12 rows and 12 input words");
 struct TcTables {
     // the part every tensor-core kernel copies (full rounds)
     uint16_t m[kTcN * kTcK];          // M of the full rounds
@@ -83,11 +87,13 @@ struct TcTables {
     // zero: the bytes of (c_0[j])^7 as fp16 subnormals, 8 identical rows per
     // core matrix, one core matrix per cell
     uint16_t a_zcap[4 * 64];
-    // the partial rounds' contractions (ChainParams)
-    uint16_t vpa[kTcN * kTcK];        // U_0 .. U_11 from y3
-    uint16_t vpb[kTcUb * 8 * kTcK];   // U_12 .. U_21 from y3 (80 rows)
-    uint16_t w1[kTcN * kTcK];         // final cells from s_0 .. s_11
-    uint16_t w2[kTcN * kTcW2 * 8];    // final cells from s_12 .. s_21 (80 columns)
+    // the partial rounds' contractions (ChainParams); input word 11 of bs, w1
+    // and w2 has zero digits (that A column holds a stale word)
+    uint16_t vpa[kTcUa * 8 * kTcK];   // U_0 .. U_9 from y3 (80 rows)
+    uint16_t vpb[kTcN * kTcK];        // U_10 .. U_21 from y3
+    uint16_t bs[kTcN * kTcK];         // rows q = 10 .. 21: beta[q][r], r = 0 .. 10 (row 21 zero)
+    uint16_t w1[kTcN * kTcK];         // final cells from s_0 .. s_10
+    uint16_t w2[kTcN * kTcK];         // final cells from s_11 .. s_21
 };
 static_assert(sizeof(TcTables) % 16 == 0, "tables are copied in 16-byte pieces");
 

@@ -17,7 +17,9 @@
 // deferred cell updates W s are contractions of round 3's S-box bytes and of
 // the 22 partial S-box outputs; only the chain c_q -> s_q = S(c_q + k_q) ->
 // c_(q+1) = U_q + sum_(r<=q) beta[q][r] s_r runs on the integer pipes, one
-// thread per state.
+// thread per state, in two halves: the first half's terms in the second
+// half's chain values are one more contraction, so each thread forms 110 of
+// the 231 products beta[q][r] s_r.
 //
 // Every fp32 sum is an exact integer below 2^24 (times 2^-24), so each result
 // is the exact residue: the same function as the integer-pipe form, bit for
@@ -37,7 +39,7 @@ constexpr int kTcAChunk = 128;                  // bytes of one 8 x 8 fp16 core 
 constexpr int kTcAChunks = kTcK / 8;            // core-matrix columns of A (12 input words)
 constexpr int kTcABytes = kTcGroup * kTcK * 2;  // A operand of a group: 24 KiB
 constexpr int kTcRegion = 128;                  // tensor-memory columns of one group
-constexpr int kTcUStore = kTcN;                 // columns 96..119 of a region hold U_0 .. U_11
+constexpr int kTcUStore = kTcN;                 // columns 96..119 of a region hold chain values as words
 // tensor-memory columns one CTA of `groups` groups allocates (a power of two)
 constexpr int tc_tmem_alloc(int groups) { return groups <= 1 ? 128 : groups <= 2 ? 256 : 512; }
 // instruction descriptor: fp16 A and B, fp32 D, both K-major, M = 128, N = n
@@ -51,10 +53,11 @@ constexpr long long kTcWaitClocks = 4ll << 30;
 constexpr uint32_t kTabM = offsetof(TcTables, m), kTabPre = offsetof(TcTables, pre);
 constexpr uint32_t kTabBBias = offsetof(TcTables, b_bias), kTabABias = offsetof(TcTables, a_bias);
 constexpr uint32_t kTabZcap = offsetof(TcTables, a_zcap);
-constexpr uint32_t kTabVpa = offsetof(TcTables, vpa), kTabVpb = offsetof(TcTables, vpb);
+constexpr uint32_t kTabVpa = offsetof(TcTables, vpa), kTabVpb = offsetof(TcTables, vpb), kTabBs = offsetof(TcTables, bs);
 constexpr uint32_t kTabW1 = offsetof(TcTables, w1), kTabW2 = offsetof(TcTables, w2);
 constexpr size_t kTabCore = offsetof(TcTables, vpa);  // what kernels without the chain copy
-static_assert(kTabVpa % 128 == 0 && kTabVpb % 128 == 0 && kTabW1 % 128 == 0 && kTabW2 % 128 == 0 &&
+static_assert(kTabVpa % 128 == 0 && kTabVpb % 128 == 0 && kTabBs % 128 == 0 && kTabW1 % 128 == 0 &&
+                  kTabW2 % 128 == 0 &&
                   kTabBBias % 128 == 0 && kTabZcap % 128 == 0,
               "tables are 128-byte aligned");
 
@@ -190,6 +193,12 @@ __device__ __forceinline__ void tc_put(const TcGroup &G, int j, uint64_t y) {
     *reinterpret_cast<uint4 *>(G.a + ((G.t >> 3) * kTcAChunks + j) * kTcAChunk + (G.t & 7) * 16) = v;
 }
 
+// The word y that tc_put wrote to row t's chunk j (the low byte of each fp16).
+__device__ __forceinline__ uint64_t tc_get(const TcGroup &G, int j) {
+    const uint4 v = *reinterpret_cast<const uint4 *>(G.a + ((G.t >> 3) * kTcAChunks + j) * kTcAChunk + (G.t & 7) * 16);
+    return ((uint64_t)__byte_perm(v.z, v.w, 0x6420) << 32) | __byte_perm(v.x, v.y, 0x6420);
+}
+
 // One contraction into the group's D (columns 0 .. n-1): the group meets
 // (its A stores visible to the tensor cores, its earlier tensor-memory
 // accesses done), thread 0 issues the bias block (when `bias`: D starts at
@@ -243,61 +252,55 @@ __device__ __forceinline__ bool tc_dense(TcGroup &G, uint32_t m_off, bool z, int
     return true;
 }
 
-// The 22 partial rounds in their unrolled form, after round 3's dense layer
-// (A still holds round 3's S-box bytes y3, x holds x^(0) = P y3).
-__device__ __forceinline__ bool tc_partial(TcGroup &G, uint64_t (&x)[kT]) {
-    const uint32_t lane_base = G.tmem + ((uint32_t)(G.t & ~31) << 16);
-    // U_0 .. U_11, kept as words in columns 96..119 of the group's region
-    if (!tc_contract(G, kTabVpa, kTcAChunks, kTcN, 6, true, false)) return false;
+// One half of the chain: s_q = S(c + k_q) for q = q0 .. q1 - 1, each into
+// A's chunk q - q0; between them c = U_q + sum_(r = q0 .. q) beta[q][r] s_r,
+// U_q the word in tensor-memory column kTcUStore + 2 (q - u0).
+__device__ __forceinline__ void chain_half(const TcGroup &G, uint32_t lane_base, uint64_t c, int q0, int q1, int u0) {
+#pragma unroll 1
+    for (int q = q0;; ++q) {
+        tc_put(G, q - q0, sbox(add_canon(c, c_dev.part_rc[q])));
+        if (q == q1 - 1) break;
+        Acc A;
+        acc_init(A, tmem_ld_word(lane_base + kTcUStore + 2 * (q - u0)));
+#pragma unroll 1
+        for (int r = q0; r <= q; ++r) acc_mac(A, tc_get(G, r - q0), c_beta[q][r]);
+        c = acc_reduce(A);
+    }
+}
+
+// Rows 0 .. rows-1 of D combined into words, stored at tensor-memory columns
+// kTcUStore + 2 i.
+template <int ROWS>
+__device__ __forceinline__ void tc_store_rows(uint32_t lane_base) {
 #pragma unroll
-    for (int i = 0; i < kT; i += 2) {
+    for (int i = 0; i < ROWS; i += 2) {
         uint32_t w[16];
         tmem_ld16(lane_base + 8 * i, w);
         tmem_st_words(lane_base + kTcUStore + 2 * i, tc_combine(w), tc_combine(w + 8));
     }
     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-    // U_12 .. U_21 as column sums in D columns 0..79
-    if (!tc_contract(G, kTabVpb, kTcAChunks, kTcUb * 8, 6, true, false)) return false;
-    // the chain; s_q in A (free now) as plain words, sst[q * 128]
-    uint64_t *sst = reinterpret_cast<uint64_t *>(G.a) + G.t;
-    uint64_t c = x[0];
-#pragma unroll 1
-    for (int q = 0;; ++q) {
-        const uint64_t s = sbox(add_canon(c, c_dev.part_rc[q]));
-        sst[q * kTcGroup] = s;
-        if (q == kRP - 1) break;
-        uint64_t u;
-        if (q < kT) {
-            u = tmem_ld_word(lane_base + kTcUStore + 2 * q);
-        } else {
-            uint32_t w[8];
-            tmem_ld8(lane_base + 8 * (q - kT), w);
-            u = tc_combine(w);
-        }
-        Acc A;
-        acc_init(A, u);
-#pragma unroll 1
-        for (int r = 0; r <= q; ++r) acc_mac(A, sst[r * kTcGroup], c_beta[q][r]);
-        c = acc_reduce(A);
-    }
-    uint64_t u21;
-    {
-        uint32_t w[8];
-        tmem_ld8(lane_base + 8 * (kRP - 1 - kT), w);
-        u21 = tc_combine(w);
-    }
-    // the deferred updates W s: s_0 .. s_11, then s_12 .. s_21, into one sum
-    uint64_t sv[kRP];
-#pragma unroll
-    for (int r = 0; r < kRP; ++r) sv[r] = sst[r * kTcGroup];
-    group_sync(G.bar);  // every thread has its s before A's rows are overwritten
-#pragma unroll
-    for (int j = 0; j < kT; ++j) tc_put(G, j, sv[j]);
+}
+
+// The 22 partial rounds in their unrolled form, after round 3's dense layer
+// (A still holds round 3's S-box bytes y3, x holds x^(0) = P y3).
+__device__ __forceinline__ bool tc_partial(TcGroup &G, uint64_t (&x)[kT]) {
+    const uint32_t lane_base = G.tmem + ((uint32_t)(G.t & ~31) << 16);
+    // U_0 .. U_9 as words
+    if (!tc_contract(G, kTabVpa, kTcAChunks, kTcUa * 8, 6, true, false)) return false;
+    tc_store_rows<kTcUa>(lane_base);
+    // U_10 .. U_21 as column sums in D (A still holds y3)
+    if (!tc_contract(G, kTabVpb, kTcAChunks, kTcN, 6, true, false)) return false;
+    // first half: s_0 .. s_10 into A's chunks 0..10
+    chain_half(G, lane_base, x[0], 0, kTcSplit, 0);
+    // D += their terms in c_11 .. c_21: the second half's U'_q (q = 10 .. 20) and U_21, as words
+    if (!tc_contract(G, kTabBs, kTcAChunks, kTcN, 6, false, false)) return false;
+    tc_store_rows<kT>(lane_base);
+    // the deferred updates W s, from s_0 .. s_10 now, s_11 .. s_21 after the second half
     if (!tc_contract(G, kTabW1, kTcAChunks, kTcN, 6, true, false)) return false;
-#pragma unroll
-    for (int j = 0; j < kTcW2; ++j) tc_put(G, j, sv[kT + j]);
-    if (!tc_contract(G, kTabW2, kTcW2, kTcN, kTcW2 / 2, false, false)) return false;
+    chain_half(G, lane_base, tmem_ld_word(lane_base + kTcUStore), kTcSplit, kRP, kTcUa);
+    if (!tc_contract(G, kTabW2, kTcAChunks, kTcN, 6, false, false)) return false;
     // cell 0 = c_22 = U_21 + (W s)_0, cell i = x_i^(0) + (W s)_i
+    const uint64_t u21 = tmem_ld_word(lane_base + kTcUStore + 2 * (kRP - 1 - kTcUa));
 #pragma unroll
     for (int i = 0; i < kT; i += 2) {
         uint32_t w[16];

@@ -26,8 +26,9 @@ pg = pytest.importorskip("paper_2506_09505_gb300")
 P = 0xFFFFFFFF00000001
 T = 12
 RP = 22
+SPLIT = 11  # the chain's first half: s_0 .. s_10
 TABLES = [("m", 12, 12), ("pre", 12, 12), ("b_bias", None, None), ("a_bias", None, None), ("a_zcap", None, None),
-          ("vpa", 12, 12), ("vpb", 10, 12), ("w1", 12, 12), ("w2", 12, 10)]
+          ("vpa", 10, 12), ("vpb", 12, 12), ("bs", 12, 12), ("w1", 12, 12), ("w2", 12, 12)]
 
 
 def half_to_float(h: int) -> float:
@@ -123,18 +124,31 @@ def test_digit_tables_reproduce_every_contraction(params):
     opt = pg.params_export_optimized()
     vp, beta, w = pg.params_export_chain()
     magic = bias_magic(t)
-    cases = [("m", opt["mds"], 12), ("pre", opt["pre"], 12), ("vpa", vp[:12], 12), ("vpb", vp[12:], 12)]
+    cases = [("m", opt["mds"], 12), ("pre", opt["pre"], 12), ("vpa", vp[:SPLIT - 1], 12)]
     for name, mat, k in cases:
         dig = decode(t[name], len(mat), k)
         assert dig.min() >= -128 and dig.max() <= 127
         worst_window([dig], magic)
         for x in _inputs(k, 0x7C00):
             assert contract([dig], magic, [x]) == plain(mat, x), name
-    # the final updates: two tables into one accumulator
-    d1, d2 = decode(t["w1"], 12, 12), decode(t["w2"], 12, 10)
+    # input word 11 of bs, w1 and w2 meets a stale A column: its digits are zero
+    stale = pg_synth.words(0x7E00, 1, bound=None)
+    # the second half's chain values: U_q (q = 10 .. 21) from y3 plus, in the
+    # same accumulator, beta[q][r] s_r for the first half's r = 0 .. 10 (row 21: none)
+    bmat = [[int(beta[q, r]) if (q < 21 and r < SPLIT) else 0 for r in range(12)] for q in range(SPLIT - 1, 22)]
+    dv, db = decode(t["vpb"], 12, 12), decode(t["bs"], 12, 12)
+    worst_window([dv, db], magic)
+    for y3, s in zip(_inputs(12, 0x7D00), _inputs(12, 0x7D80)):
+        s = np.concatenate([s[:SPLIT], stale])
+        want = [(a + b) % P for a, b in zip(plain(vp[SPLIT - 1:], y3), plain(bmat, s[:SPLIT]))]
+        assert contract([dv, db], magic, [y3, s]) == want
+    # the final updates: s_0 .. s_10 and s_11 .. s_21 into one accumulator
+    d1, d2 = decode(t["w1"], 12, 12), decode(t["w2"], 12, 12)
     worst_window([d1, d2], magic)
     for s in _inputs(22, 0x7D00):
-        assert contract([d1, d2], magic, [s[:12], s[12:]]) == plain(w, s)
+        s1 = np.concatenate([s[:SPLIT], stale])
+        s2 = np.concatenate([s[SPLIT:], stale])
+        assert contract([d1, d2], magic, [s1, s2]) == plain(w, s)
     pg.params_select(None)
 
 
@@ -153,8 +167,12 @@ def test_zero_capacity_pattern_is_the_constant_sbox_outputs():
             assert got == c7
 
 
-def _chain_permute(x, op, vp, beta, w):
-    """Alg. 1 with the partial rounds in their unrolled form (Python integers)."""
+def _chain_permute(x, op, vp, beta, w, split=None):
+    """Alg. 1 with the partial rounds in their unrolled form (Python integers).
+
+    split: the chain in two halves as the kernels run it -- the first half's
+    terms beta[q][r] s_r (r < split) of the later chain values are added to
+    U_q in one step after s_(split-1), the rest as the chain goes."""
     x = [int(v) % P for v in x]
     fr, M, pre = op["full_rc"], op["mds"], op["pre"]
 
@@ -171,8 +189,12 @@ def _chain_permute(x, op, vp, beta, w):
     c, s = x0[0], []
     for q in range(RP):
         s.append(pow((c + int(op["part_rc"][q])) % P, 7, P))
+        if split is not None and q == split - 1:
+            u = u[:split - 1] + [(u[p] + sum(int(beta[p, r]) * s[r] for r in range(split))) % P
+                                 for p in range(split - 1, RP - 1)] + [u[RP - 1]]
         if q < RP - 1:
-            c = (u[q] + sum(int(beta[q, r]) * s[r] for r in range(q + 1))) % P
+            lo = split if (split is not None and q >= split - 1) else 0
+            c = (u[q] + sum(int(beta[q, r]) * s[r] for r in range(lo, q + 1))) % P
     ws = [sum(int(w[i, r]) * s[r] for r in range(RP)) % P for i in range(12)]
     x = [(u[RP - 1] + ws[0]) % P] + [(x0[i] + ws[i]) % P for i in range(1, 12)]
     for r in range(4, 8):
@@ -194,5 +216,6 @@ def test_unrolled_partial_rounds_equal_the_plain_permutation(params):
         want = oracle.permute(st, rc=rc, mds=mds)
         for k in range(st.shape[0]):
             assert _chain_permute(st[k], op, vp, beta, w) == [int(v) for v in want[k]]
+            assert _chain_permute(st[k], op, vp, beta, w, split=SPLIT) == [int(v) for v in want[k]]
     finally:
         pg.params_select(None)
