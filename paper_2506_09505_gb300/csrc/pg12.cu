@@ -437,24 +437,26 @@ __device__ __forceinline__ bool tc_unit(TcGroup &G, const TreePlan &tp, uint32_t
     const uint64_t n = tp.n_leaves, cnt = n >> l;
     const uint64_t k = u * kTcGroup + G.t;
     const bool valid = k < cnt;
+    // a node is the one-chunk sponge of its children's 8 words; one
+    // permutation call site for leaves and nodes keeps the kernel's code small
+    const bool leaf = l == 0;
+    const uint64_t w = leaf ? tp.width : 2 * kDigest, chunks = (w + kRate - 1) / kRate;
+    const uint64_t *row = leaf ? tp.rows + (valid ? k : 0) * w
+                               : tp.nodes + kDigest * (level_off(n, l - 1) + 2 * (valid ? k : 0));
     uint64_t x[kT];
 #pragma unroll
     for (int i = kRate; i < kT; ++i) x[i] = 0;
-    if (l == 0) {
-        const uint64_t w = tp.width, chunks = (w + kRate - 1) / kRate;
-        const uint64_t *row = tp.rows + (valid ? k : 0) * w;
-        for (uint64_t c = 0; c < chunks; ++c) {
-            uint64_t ch[kRate];
+    for (uint64_t c = 0; c < chunks; ++c) {
+        uint64_t ch[kRate];
+        if (leaf) {
             load_chunk(row, w, c, tp.vec16 != 0, ch);
+        } else {  // written by this launch: coherent loads
 #pragma unroll
-            for (int i = 0; i < kRate; ++i) x[i] = valid ? ch[i] : 0ull;
-            if (!tc_permute<kTcChain>(G, x, c == 0, c + 1 == chunks)) return false;
+            for (int i = 0; i < kRate; i += 2) ld2_cg(row + i, ch[i], ch[i + 1]);
         }
-    } else {
-        const uint64_t *kids = tp.nodes + kDigest * (level_off(n, l - 1) + 2 * (valid ? k : 0));
 #pragma unroll
-        for (int i = 0; i < 2 * kDigest; i += 2) ld2_cg(kids + i, x[i], x[i + 1]);
-        if (!tc_permute<kTcChain>(G, x, true, true)) return false;
+        for (int i = 0; i < kRate; ++i) x[i] = valid ? ch[i] : 0ull;
+        if (!tc_permute<kTcChain>(G, x, c == 0, c + 1 == chunks)) return false;
     }
     if (valid) {
         uint64_t *dst = tp.nodes + kDigest * (level_off(n, l) + k);
