@@ -171,13 +171,16 @@ const char *pg_params_name(void);
  * bit-identical):
  *   PG_ENGINE_INT     every step on the integer pipes (Alg. 1 with the
  *                     special-prime reduction of Alg. 2, one thread per state);
- *   PG_ENGINE_TENSOR  the same, except that the 12x12 MDS products of the
- *                     eight full rounds (Alg. 1, MDS) of 128 states at a time
- *                     are one exact tensor-core contraction of byte limbs
- *                     (fp16 operands, fp32 sums of integers below 2^24) --
- *                     used by pg_permute_batch, pg_hash_rows, the leaves of
- *                     pg_merkle_build / pg_merkle_build_host and their tree
- *                     levels of at least 2^13 nodes.  The default.
+ *   PG_ENGINE_TENSOR  the same function, with every linear layer of 128
+ *                     states at a time as an exact tensor-core contraction of
+ *                     byte limbs (fp16 operands, fp32 sums of integers below
+ *                     2^24): the eight full rounds' 12x12 MDS products (Alg. 1,
+ *                     MDS) and the 22 partial rounds' layers in their unrolled
+ *                     form (pg_params_export_chain), the S-boxes and a scalar
+ *                     chain on the integer pipes -- used by pg_permute_batch,
+ *                     pg_hash_rows, the leaves of pg_merkle_build /
+ *                     pg_merkle_build_host and their tree levels of at least
+ *                     2^13 nodes.  The default.
  * pg_set_engine applies to launches made after it returns; PG_ERR_INVALID_ARG
  * for any other value.  Host-only.
  */
@@ -201,10 +204,12 @@ int pg_get_engine(void);
  *   b_bias [2 core matrices]  row b, column 0 = 4 u_b (the bias digits)
  *   a_bias [2 core matrices]  2^-13 at column 0 of every row
  *   a_zcap [4 core matrices]  bytes of (c_0[j])^7, j = 8..11, every row
- *   vpa  [96 x 96]  rows 0..11 of the chain's vp (pg_params_export_chain)
- *   vpb  [80 x 96]  rows 12..21 of vp
- *   w1   [96 x 96]  the chain's w, inputs s_0 .. s_11
- *   w2   [96 x 80]  w, inputs s_12 .. s_21
+ *   vpa  [80 x 96]  rows 0..9 of the chain's vp (pg_params_export_chain)
+ *   vpb  [96 x 96]  rows 10..21 of vp
+ *   bs   [96 x 96]  row i: beta[10 + i][r] for inputs r = 0..10; row 11
+ *                   and input 11 zero
+ *   w1   [96 x 96]  the chain's w, inputs s_0 .. s_10 (input 11 zero)
+ *   w2   [96 x 96]  w, inputs s_11 .. s_21 (input 11 zero)
  * Host-only; works without a GPU.
  */
 size_t pg_tc_tables_export(void *out, size_t bytes);
