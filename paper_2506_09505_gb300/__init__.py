@@ -232,7 +232,9 @@ ENGINE_INT, ENGINE_TENSOR = 0, 1
 
 
 def set_engine(engine: int) -> None:
-    """Permutation engine of later launches: ENGINE_TENSOR (default) or ENGINE_INT."""
+    """Permutation engine of later launches: ENGINE_TENSOR (default, the
+    linear layers as exact tensor-core contractions) or ENGINE_INT (integer
+    pipes only)."""
     _check(load().pg_set_engine(int(engine)))
 
 

@@ -120,6 +120,14 @@ __device__ __forceinline__ uint64_t fold(uint64_t lo, uint64_t hi, uint32_t k) {
 
 __device__ __forceinline__ uint64_t reduce128(u128 r) { return fold((uint64_t)r, (uint64_t)(r >> 64), 0); }
 
+// a * b + c for 32-bit a, b and a 64-bit c (one IMAD.WIDE; the caller keeps
+// the sum below 2^64)
+__device__ __forceinline__ uint64_t madw(uint32_t a, uint32_t b, uint64_t c) {
+    uint64_t d;
+    asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
+    return d;
+}
+
 __device__ __forceinline__ uint64_t canon(uint64_t x) { return x >= P ? x - P : x; }
 
 // (Summing the columns inside chained 32x32+64-bit multiply-adds instead of

@@ -370,8 +370,7 @@ void digit_table(const uint64_t *mat, int n, int k, uint16_t *dst, long *pos, lo
 
 }  // namespace
 
-bool build_tc_tables(const OptParams &op, TcTables &tt) {
-    std::memset(&tt, 0, sizeof tt);
+void tc_bias_blocks(uint16_t a_bias[128], uint16_t b_bias[128], int u[8]) {
     // Bias digits u_b: column (i, b) reads back bits = 0x3E800000 + magic_b + Z
     // with magic_b = 8192 u_b (A bias 2^-13 times B bias 4 u_b, values scaled by
     // 2^-24), and sum_b 2^(8b) (0x3E800000 + 8192 u_b) = 0 (mod p) is solved for
@@ -388,7 +387,6 @@ bool build_tc_tables(const OptParams &op, TcTables &tt) {
     const u128 umin = (u128)1407 * G;
     const uint64_t umin_p = (uint64_t)(umin % kP);
     u128 rest = fp_sub(t, umin_p);                               // U - umin, in [0, p)
-    int u[8];
     for (int b = 7; b >= 0; --b) {
         const u128 wgt = (u128)1 << (8 * b);
         u128 e = rest / wgt;
@@ -396,8 +394,16 @@ bool build_tc_tables(const OptParams &op, TcTables &tt) {
         rest -= e * wgt;
         u[b] = 1407 + (int)e;
     }
-    for (int b = 0; b < 8; ++b) tt.b_bias[b * 8] = half_of_int(4 * u[b]);
-    for (int r = 0; r < 8; ++r) tt.a_bias[r * 8] = 0x0800;  // 2^-13
+    std::memset(a_bias, 0, 128 * sizeof(uint16_t));
+    std::memset(b_bias, 0, 128 * sizeof(uint16_t));
+    for (int b = 0; b < 8; ++b) b_bias[b * 8] = half_of_int(4 * u[b]);
+    for (int r = 0; r < 8; ++r) a_bias[r * 8] = 0x0800;  // 2^-13
+}
+
+bool build_tc_tables(const OptParams &op, TcTables &tt) {
+    std::memset(&tt, 0, sizeof tt);
+    int u[8];
+    tc_bias_blocks(tt.a_bias, tt.b_bias, u);
 
     ChainParams cp;
     derive_chain(op, cp);

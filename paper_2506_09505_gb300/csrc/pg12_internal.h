@@ -147,6 +147,9 @@ void derive_chain(const OptParams &op, ChainParams &cp);
 // Digit tables of the tensor-core contractions for an optimised set; false if
 // a sum could leave the exact window (every table is checked).
 bool build_tc_tables(const OptParams &op, TcTables &tt);
+// The bias blocks every tensor-core contraction adds (TcTables::a_bias and
+// b_bias) and their digits u_b.
+void tc_bias_blocks(uint16_t a_bias[128], uint16_t b_bias[128], int u[8]);
 // FIPS 180-4 SHA-256 of `len` bytes as 64 lowercase hex digits.
 void sha256_hex(const uint8_t *data, size_t len, char out[65]);
 }  // namespace host

@@ -133,11 +133,6 @@ __device__ __forceinline__ void dense_phase(uint64_t *slot, int m, int rows = kT
 // x_j * m for m < 2^8 is two 32x8-bit products; twelve of them fit 64 bits,
 // so both halves accumulate through the IMAD.WIDE addend with no carries and
 // one fold per output.
-__device__ __forceinline__ uint64_t madw(uint32_t a, uint32_t b, uint64_t c) {
-    uint64_t d;
-    asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
-    return d;
-}
 
 template <int S, int NT = kT>
 __device__ __forceinline__ void dense_small_phase(uint64_t *slot, int rows = kT) {
