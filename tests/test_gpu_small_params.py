@@ -1,6 +1,8 @@
 """GPU parity with the small-entry parameter set pg12_small (circulant MDS
-with 8-bit entries, Table 1's mult_72 / mmult_4x12_8 shape): the dense
-layers take the specialised path, every output must equal the oracle."""
+with 8-bit entries, Table 1's mult_72 / mmult_4x12_8 shape), on both engines:
+the integer engine's dense layers take the specialised 8-bit path, the
+tensor engine's digit tables are built from the small matrix like from any
+other; every output must equal the oracle."""
 import numpy as np
 import pytest
 
@@ -20,6 +22,15 @@ def small_set():
     yield
     torch.cuda.synchronize()
     pg.params_select(None)
+    pg.set_engine(pg.ENGINE_TENSOR)
+
+
+@pytest.fixture(params=["tensor", "int"], autouse=True)
+def engine(request):
+    pg.set_engine(pg.ENGINE_TENSOR if request.param == "tensor" else pg.ENGINE_INT)
+    yield request.param
+    torch.cuda.synchronize()
+    pg.set_engine(pg.ENGINE_TENSOR)
 
 
 def _dev(a):
