@@ -24,7 +24,10 @@
  *     NULL = the legacy default stream) unless stated otherwise.  Argument
  *     errors are detected on the host and returned before anything is
  *     launched.  CUDA errors map to PG_ERR_CUDA; pg_last_error() gives the
- *     text.  Nothing in the library spins on the device.
+ *     text.  Device-side waits (on the tensor cores' completion barriers and
+ *     on pg_merkle_build_host's chunk arrival counter) give up after about
+ *     2 s and report through pg_device_faults; nothing else waits on the
+ *     device.
  *   - Not thread-safe: calls that share one pg_init() context must be
  *     serialised by the caller.
  */
@@ -334,8 +337,12 @@ pg_status pg_merkle_build(const uint64_t *rows, size_t n_leaves, size_t width, u
 /*
  * pg_merkle_build_host -- pg_merkle_build with the rows in host memory: the
  * same nodes, with the host-to-device copy of the rows overlapped with leaf
- * hashing (the rows are copied in at most 11 growing chunks on a library stream and
- * each chunk's leaves are hashed on `stream` as soon as it has arrived).
+ * hashing.  The rows are copied in at most 11 growing chunks on a library
+ * stream.  Tensor engine: one leaf launch on `stream` hashes them as they
+ * arrive (after each chunk the copy stream writes an arrival counter that
+ * the launch waits on, each wait bounded by about 2 s, then the fault shows
+ * in pg_device_faults); integer engine: one leaf launch per chunk once its
+ * copy has finished.
  *   rows_host  host, n_leaves*width words, row-major; page-locked memory
  *              lets the copies overlap (pageable memory works, serialised).
  *   rows_dev   dev, n_leaves*width words: caller-owned staging buffer the
@@ -344,7 +351,7 @@ pg_status pg_merkle_build(const uint64_t *rows, size_t n_leaves, size_t width, u
  * Rows of less than 64 MiB are copied in one piece before the build.
  * The copies start once the work already queued on `stream` has finished.
  * Allocates nothing.  Calls from several host threads at once are not
- * supported (they share the library's copy stream and events).
+ * supported (they share the library's copy stream, events and counter).
  */
 pg_status pg_merkle_build_host(const uint64_t *rows_host, size_t n_leaves, size_t width, uint64_t *rows_dev,
                                uint64_t *nodes, uint64_t *root_out, void *stream);

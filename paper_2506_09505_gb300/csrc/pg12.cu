@@ -104,6 +104,19 @@ __device__ __forceinline__ void load_chunk(const uint64_t *row, uint64_t w, uint
     }
 }
 
+// The same, through L2 only: for rows written while the kernel runs.
+__device__ __forceinline__ void load_chunk_cg(const uint64_t *row, uint64_t w, uint64_t c, bool vec16,
+                                              uint64_t (&ch)[kRate]) {
+    const uint64_t base = c * kRate;
+    if (base + kRate <= w && vec16) {
+#pragma unroll
+        for (int i = 0; i < kRate; i += 2) ld2_cg(row + base + i, ch[i], ch[i + 1]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < kRate; ++i) ch[i] = (base + i < w) ? __ldcg(row + base + i) : 0ull;
+    }
+}
+
 // Overwrite-mode sponge over one row in the thread's state slot; returns
 // with the (weak) final state in the slot.
 template <int S, int MDS>
@@ -197,15 +210,16 @@ __global__ void __launch_bounds__(kSmallBlock) k_merkle_level(const uint64_t *__
 
 // ------------------------------------------------- tensor-core kernels
 // Persistent kernels of kTcGroups groups of 128 threads (one CTA per SM:
-// its tables and operands take 199 KB of shared memory, its groups 128
-// columns of tensor memory each; every thread keeps its state in registers).
+// its digit tables (124 KB) and the groups' A operands take 225 KB of shared
+// memory, its groups 128 columns of tensor memory each; every thread keeps
+// its state in registers).
 // Group q of CTA c takes units c * kTcGroups + q, then every
 // gridDim.x * kTcGroups-th after: a static schedule with no shared counter,
 // so launches on different streams are independent.  A unit is 128
 // consecutive states or rows; rows past the end are computed on zeros and
 // not stored.
 // PG12_TC_CHAIN 1 (default): the partial rounds in their unrolled form on the
-// tensor cores (tc_partial, 105 KB of tables); 0: on the integer pipes.
+// tensor cores (tc_partial, 87 KB of the tables); 0: on the integer pipes.
 #ifndef PG12_TC_CHAIN
 #define PG12_TC_CHAIN 1
 #endif
@@ -281,6 +295,76 @@ __global__ void __launch_bounds__(kTcGroup * GROUPS, 1) k_tc_sponge(const uint64
 #pragma unroll
             for (int i = 0; i < kRate; ++i) x[i] = valid ? ch[i] : 0ull;
             ok = tc_permute<CHAIN>(G, x, c == 0, c + 1 == chunks);
+        }
+        if (!ok) break;
+        if (valid) {
+            st2(out + kDigest * r, canon(x[0]), canon(x[1]));
+            st2(out + kDigest * r + 2, canon(x[2]), canon(x[3]));
+        }
+    }
+    tc_teardown<GROUPS, CHAIN>(tc_sm, G);
+}
+
+// Leaf sponges over rows that arrive in chunks while the kernel runs
+// (pg_merkle_build_host): rows [end[c-1], end[c]) are chunk c, and the copy
+// stream writes base + c + 1 into *ready once chunk c is in device memory.
+// Before a unit's rows are read, thread 0 of its group waits (bounded, with
+// an acquire load) until *ready shows the chunk of the unit's last row; the
+// group's barrier passes that on, and the rows are read through L2.  Units
+// go out in increasing order, so the first chunks are hashed while later
+// ones are still being copied, in one launch.
+struct ChunkMap {
+    uint64_t end[16];
+    uint32_t count;
+    uint32_t base;
+};
+
+__device__ __forceinline__ bool wait_ready(const uint32_t *ready, uint32_t want) {
+    const long long t0 = clock64();
+    for (;;) {
+        uint32_t v;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ready) : "memory");
+        if ((int32_t)(v - want) >= 0) return true;  // serial-number order: base wraps
+        if (clock64() - t0 > kTcWaitClocks) return false;
+        __nanosleep(200);
+    }
+}
+
+template <int GROUPS, bool CHAIN>
+__global__ void __launch_bounds__(kTcGroup * GROUPS, 1)
+    k_tc_leaves_stream(const uint64_t *__restrict__ rows, uint64_t n, uint64_t w, int vec16,
+                       uint64_t *__restrict__ out, const uint32_t *__restrict__ ready, const ChunkMap cm) {
+    extern __shared__ __align__(1024) uint8_t tc_sm[];
+    TcGroup G = tc_setup<GROUPS, CHAIN>(tc_sm);
+    const uint64_t units = (n + kTcGroup - 1) / kTcGroup;
+    const uint64_t step = (uint64_t)gridDim.x * GROUPS;
+    const uint64_t chunks = (w + kRate - 1) / kRate;
+    uint32_t have = 0;  // chunks this group has seen arrive
+    for (uint64_t u = (uint64_t)blockIdx.x * GROUPS + threadIdx.x / kTcGroup; u < units; u += step) {
+        const uint64_t last = (u + 1) * kTcGroup < n ? (u + 1) * kTcGroup - 1 : n - 1;
+        uint32_t c = 0;
+        while (c + 1 < cm.count && cm.end[c] <= last) ++c;
+        if (c >= have) {
+            const uint32_t late = G.t == 0 && !wait_ready(ready, cm.base + c + 1);
+            if (group_sync_or(G.bar, late)) {
+                G.failed = 1;
+                break;
+            }
+            have = c + 1;
+        }
+        const uint64_t r = u * kTcGroup + G.t;
+        const bool valid = r < n;
+        const uint64_t *row = rows + (valid ? r : 0) * w;
+        uint64_t x[kT];
+#pragma unroll
+        for (int i = kRate; i < kT; ++i) x[i] = 0;
+        bool ok = true;
+        for (uint64_t k = 0; k < chunks && ok; ++k) {
+            uint64_t ch[kRate];
+            load_chunk_cg(row, w, k, vec16 != 0, ch);
+#pragma unroll
+            for (int i = 0; i < kRate; ++i) x[i] = valid ? ch[i] : 0ull;
+            ok = tc_permute<CHAIN>(G, x, k == 0, k + 1 == chunks);
         }
         if (!ok) break;
         if (valid) {
@@ -754,6 +838,8 @@ namespace {
 #define PG12_TC_SMALL_TREE 8192
 #endif
 
+constexpr uint32_t kReadyVals = 1u << 16;  // values of the chunk arrival counter
+
 struct Context {
     bool params_ready = false;
     int params_set = 0;  // 0 = pg12_v1, 1 = pg12_small
@@ -776,6 +862,12 @@ struct Context {
     uint64_t tc_min_nodes = PG12_TC_MIN_NODES;  // smallest tree level built by the tensor-core kernel
     cudaStream_t copy_st = nullptr;  // host-row copies of pg_merkle_build_host
     cudaEvent_t host_ev[17] = {};    // one per chunk, plus "previous work done"
+    // chunk arrival counter of the streaming leaf launch: the copy stream
+    // copies ready_vals[v] = v into *d_ready; every build takes 16 new values
+    uint32_t *d_ready = nullptr;
+    uint32_t *ready_vals = nullptr;  // page-locked, kReadyVals entries
+    uint32_t ready_base = 0;
+    cudaEvent_t ready_ev = nullptr;  // after the last streaming leaf launch
 };
 Context g;
 std::mutex g_mu;
@@ -1096,6 +1188,24 @@ pg_status launch_tc_sponge(const uint64_t *rows, uint64_t n, uint64_t w, uint64_
     ProfScope prof(kid, st, n * ((w + kRate - 1) / kRate));
     if (one) PG_CUDA(cudaLaunchKernelEx(&cfg, dev::k_tc_sponge<1, false>, rows, n, w, vec16, out));
     else PG_CUDA(cudaLaunchKernelEx(&cfg, dev::k_tc_sponge<dev::kTcGroups, dev::kTcChain>, rows, n, w, vec16, out));
+    return PG_OK;
+}
+
+// The leaf launch of a streamed host-rows build (k_tc_leaves_stream), in
+// the same CTA shapes as launch_tc_sponge.
+pg_status launch_leaves_stream(const uint64_t *rows, uint64_t n, uint64_t w, uint64_t *out, const uint32_t *ready,
+                               const dev::ChunkMap &cm, cudaStream_t st) {
+    const int vec16 = ((w % 2) == 0 && (reinterpret_cast<uintptr_t>(rows) % 16) == 0) ? 1 : 0;
+    const uint64_t units = (n + dev::kTcGroup - 1) / dev::kTcGroup;
+    const bool one = units < (uint64_t)g.sms * dev::kTcGroups;
+    ProfScope prof(kIdTcLeaves, st, n * ((w + kRate - 1) / kRate));
+    if (one)
+        dev::k_tc_leaves_stream<1, false><<<(unsigned)units, dev::kTcGroup, dev::TcL1::kBytes, st>>>(rows, n, w, vec16, out,
+                                                                                                  ready, cm);
+    else
+        dev::k_tc_leaves_stream<dev::kTcGroups, dev::kTcChain>
+            <<<tc_grid(n), dev::kTcThreads, dev::TcL::kBytes, st>>>(rows, n, w, vec16, out, ready, cm);
+    PG_CUDA(cudaGetLastError());
     return PG_OK;
 }
 
@@ -1652,6 +1762,10 @@ pg_status pg_init(int device, const char *params_path) {
     PG_CUDA(cudaFuncSetAttribute(dev::k_tc_sponge<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)dev::TcL1::kBytes));
     PG_CUDA(cudaFuncSetAttribute(dev::k_tc_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dev::TcL::kBytes));
+    PG_CUDA(cudaFuncSetAttribute(dev::k_tc_leaves_stream<dev::kTcGroups, dev::kTcChain>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dev::TcL::kBytes));
+    PG_CUDA(cudaFuncSetAttribute(dev::k_tc_leaves_stream<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)dev::TcL1::kBytes));
     {
         const int ns = ntt_upload_constants();
         if (ns != PG_OK) return (pg_status)ns;
@@ -1687,6 +1801,12 @@ pg_status pg_init(int device, const char *params_path) {
     g.ws_bytes = kWorkspaceBytes;
     PG_CUDA(cudaStreamCreateWithFlags(&g.copy_st, cudaStreamNonBlocking));
     for (auto &ev : g.host_ev) PG_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    PG_CUDA(cudaMalloc(&g.d_ready, 256));
+    PG_CUDA(cudaMemset(g.d_ready, 0, 256));
+    PG_CUDA(cudaHostAlloc(&g.ready_vals, kReadyVals * sizeof(uint32_t), cudaHostAllocDefault));
+    for (uint32_t v = 0; v < kReadyVals; ++v) g.ready_vals[v] = v;
+    g.ready_base = 0;
+    PG_CUDA(cudaEventCreateWithFlags(&g.ready_ev, cudaEventDisableTiming));
     g.device = device;
     g.init = true;
     return PG_OK;
@@ -1704,6 +1824,12 @@ pg_status pg_shutdown(void) {
         if (ev) cudaEventDestroy(ev);
         ev = nullptr;
     }
+    if (g.d_ready) cudaFree(g.d_ready);
+    g.d_ready = nullptr;
+    if (g.ready_vals) cudaFreeHost(g.ready_vals);
+    g.ready_vals = nullptr;
+    if (g.ready_ev) cudaEventDestroy(g.ready_ev);
+    g.ready_ev = nullptr;
     g.init = false;
     g.device = -1;
     return PG_OK;
@@ -1804,6 +1930,9 @@ pg_status pg_merkle_build(const uint64_t *rows, size_t n_leaves, size_t width, u
 
 // Host-row builds: the first copied chunk holds n / FIRST_DIV rows, each next
 // one twice as many, up to n / MAX_DIV; the 16th takes the rest.
+#ifndef PG12_HOST_STREAM
+#define PG12_HOST_STREAM 1  // 0: one leaf launch per copied chunk (the tensor engine's earlier form)
+#endif
 #ifndef PG12_HOST_CHUNK_FIRST_DIV
 #define PG12_HOST_CHUNK_FIRST_DIV 64
 #endif
@@ -1842,6 +1971,49 @@ pg_status pg_merkle_build_host(const uint64_t *rows_host, size_t n_leaves, size_
     PG_CUDA(cudaStreamWaitEvent(g.copy_st, g.host_ev[16], 0));
     const uint64_t chunk_max = n / PG12_HOST_CHUNK_MAX_DIV;
     uint64_t chunk = n / PG12_HOST_CHUNK_FIRST_DIV, first = 0;
+    if (g.engine == 1 && PG12_HOST_STREAM) {
+        // Tensor engine: one leaf launch for all chunks.  After each chunk's
+        // rows the copy stream copies the arrival value base + c + 1 into
+        // d_ready (a copy-engine write; the waiting kernel needs no other
+        // kernel to run), and the launch's groups wait for the chunk of each
+        // unit before reading it.  Every build takes 16 fresh values; when
+        // they run out, the counter restarts at 0 once the last streaming
+        // launch has finished (no launch can then be waiting on it).
+        if (g.ready_base + 16 >= kReadyVals) {
+            PG_CUDA(cudaEventSynchronize(g.ready_ev));
+            PG_CUDA(cudaMemcpyAsync(g.d_ready, g.ready_vals, sizeof(uint32_t), cudaMemcpyHostToDevice, g.copy_st));
+            // this build's launch must not see the old, larger value
+            PG_CUDA(cudaEventRecord(g.host_ev[15], g.copy_st));
+            PG_CUDA(cudaStreamWaitEvent(st, g.host_ev[15], 0));
+            g.ready_base = 0;
+        }
+        dev::ChunkMap cm = {};
+        cm.base = g.ready_base;
+        for (uint32_t c = 0; first < n; ++c) {
+            const uint64_t rows_c = (chunk < n - first && c < 15) ? chunk : n - first;
+            PG_CUDA(cudaMemcpyAsync(rows_dev + first * width, rows_host + first * width, rows_c * bytes_per_row,
+                                    cudaMemcpyHostToDevice, g.copy_st));
+            PG_CUDA(cudaMemcpyAsync(g.d_ready, g.ready_vals + cm.base + c + 1, sizeof(uint32_t),
+                                    cudaMemcpyHostToDevice, g.copy_st));
+            first += rows_c;
+            cm.end[c] = first;
+            cm.count = c + 1;
+            if (chunk < chunk_max) chunk <<= 1;
+        }
+        g.ready_base += 16;
+        // the reset copy (if any) and this build's values are ordered on the
+        // copy stream; the launch itself depends on nothing but `st`
+        s = launch_leaves_stream(rows_dev, n, width, nodes, g.d_ready, cm, st);
+        if (s != PG_OK) return s;
+        PG_CUDA(cudaEventRecord(g.ready_ev, st));
+        s = launch_levels(nodes, n, 1, st);
+        if (s != PG_OK) return s;
+        if (root_out) {
+            PG_CUDA(cudaMemcpyAsync(root_out, nodes + 4 * (2 * n - 2), 32, cudaMemcpyDeviceToHost, st));
+            PG_CUDA(cudaStreamSynchronize(st));
+        }
+        return PG_OK;
+    }
     for (uint32_t c = 0; first < n; ++c) {
         // the 16th chunk takes whatever is left (16 copy events)
         const uint64_t rows_c = (chunk < n - first && c < 15) ? chunk : n - first;

@@ -55,3 +55,35 @@ def test_host_build_reuses_staging_buffer_back_to_back():
     assert torch.equal(na, pg.merkle_build(a.cuda()))
     assert torch.equal(nb, pg.merkle_build(b.cuda()))
     assert torch.equal(stage, b.cuda())
+
+
+def test_host_build_streams_its_leaves_in_one_launch():
+    # tensor engine, rows of at least 64 MiB: one leaf launch consumes the copied chunks as they land
+    n, w = 1 << 21, 8
+    rows = pg_synth.matrix_torch(0x8B00, n, w).pin_memory()
+    torch.cuda.synchronize()
+    pg.profile_enable(True)
+    nodes = pg.merkle_build_host(rows)
+    torch.cuda.synchronize()
+    kern = pg.profile_read()
+    pg.profile_enable(False)
+    assert kern["k_tc_sponge:leaves"]["launches"] == 1
+    assert torch.equal(nodes, pg.merkle_build(rows.cuda()))
+
+
+def test_host_build_arrival_counter_restarts():
+    # every streamed build takes 16 values of the chunk arrival counter, which
+    # restarts after 4096 builds; alternating two row sets makes a launch that
+    # read a chunk before it arrived hash the other set's rows
+    n, w = 1 << 20, 8
+    sets = [pg_synth.matrix_torch(0x8C00 + k, n, w).pin_memory() for k in range(2)]
+    want = [pg.merkle_build(r.cuda()) for r in sets]
+    stage = torch.empty((n, w), dtype=torch.int64, device="cuda")
+    nodes = torch.empty((2 * n - 1, 4), dtype=torch.int64, device="cuda")
+    faults = pg.device_faults()
+    for i in range(4100):
+        pg.merkle_build_host(sets[i % 2], stage, nodes)
+        if i % 512 == 0 or 4090 <= i:
+            torch.cuda.synchronize()
+            assert torch.equal(nodes, want[i % 2]), i
+    assert pg.device_faults() == 0 and faults == 0
