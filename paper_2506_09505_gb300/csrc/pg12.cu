@@ -1991,20 +1991,24 @@ pg_status pg_merkle_build_host(const uint64_t *rows_host, size_t n_leaves, size_
         cm.base = g.ready_base;
         for (uint32_t c = 0; first < n; ++c) {
             const uint64_t rows_c = (chunk < n - first && c < 15) ? chunk : n - first;
-            PG_CUDA(cudaMemcpyAsync(rows_dev + first * width, rows_host + first * width, rows_c * bytes_per_row,
-                                    cudaMemcpyHostToDevice, g.copy_st));
-            PG_CUDA(cudaMemcpyAsync(g.d_ready, g.ready_vals + cm.base + c + 1, sizeof(uint32_t),
-                                    cudaMemcpyHostToDevice, g.copy_st));
             first += rows_c;
             cm.end[c] = first;
             cm.count = c + 1;
             if (chunk < chunk_max) chunk <<= 1;
         }
         g.ready_base += 16;
-        // the reset copy (if any) and this build's values are ordered on the
-        // copy stream; the launch itself depends on nothing but `st`
+        // the launch first, so that it is on the device while the copies are
+        // still being queued; the reset copy (if any) and this build's values
+        // are ordered on the copy stream
         s = launch_leaves_stream(rows_dev, n, width, nodes, g.d_ready, cm, st);
         if (s != PG_OK) return s;
+        for (uint32_t c = 0; c < cm.count; ++c) {
+            const uint64_t lo = c ? cm.end[c - 1] : 0;
+            PG_CUDA(cudaMemcpyAsync(rows_dev + lo * width, rows_host + lo * width, (cm.end[c] - lo) * bytes_per_row,
+                                    cudaMemcpyHostToDevice, g.copy_st));
+            PG_CUDA(cudaMemcpyAsync(g.d_ready, g.ready_vals + cm.base + c + 1, sizeof(uint32_t),
+                                    cudaMemcpyHostToDevice, g.copy_st));
+        }
         PG_CUDA(cudaEventRecord(g.ready_ev, st));
         s = launch_levels(nodes, n, 1, st);
         if (s != PG_OK) return s;
