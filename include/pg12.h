@@ -342,7 +342,10 @@ pg_status pg_merkle_build(const uint64_t *rows, size_t n_leaves, size_t width, u
  * arrive (after each chunk the copy stream writes an arrival counter that
  * the launch waits on, each wait bounded by about 2 s, then the fault shows
  * in pg_device_faults); integer engine: one leaf launch per chunk once its
- * copy has finished.
+ * copy has finished.  The streamed form needs the copies to run while the
+ * launch does: tools that hold copies back during a kernel (profilers that
+ * replay kernels) make its waits run out; PG12_HOST_STREAM=0 in the
+ * environment (read by pg_init) selects the per-chunk form.
  *   rows_host  host, n_leaves*width words, row-major; page-locked memory
  *              lets the copies overlap (pageable memory works, serialised).
  *   rows_dev   dev, n_leaves*width words: caller-owned staging buffer the

@@ -36,6 +36,7 @@
 #include <unordered_map>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -838,6 +839,9 @@ namespace {
 #define PG12_TC_SMALL_TREE 8192
 #endif
 
+#ifndef PG12_HOST_STREAM
+#define PG12_HOST_STREAM 1  // 0: one leaf launch per copied chunk (also at run time: PG12_HOST_STREAM=0)
+#endif
 constexpr uint32_t kReadyVals = 1u << 16;  // values of the chunk arrival counter
 
 struct Context {
@@ -868,6 +872,11 @@ struct Context {
     uint32_t *ready_vals = nullptr;  // page-locked, kReadyVals entries
     uint32_t ready_base = 0;
     cudaEvent_t ready_ev = nullptr;  // after the last streaming leaf launch
+    // the streamed form is used when the device overlaps copies with kernels
+    // and the environment does not set PG12_HOST_STREAM=0 (tools that hold
+    // copies back while a kernel runs, such as profilers replaying kernels,
+    // would make its waits run out)
+    bool host_stream = false;
 };
 Context g;
 std::mutex g_mu;
@@ -1807,6 +1816,12 @@ pg_status pg_init(int device, const char *params_path) {
     for (uint32_t v = 0; v < kReadyVals; ++v) g.ready_vals[v] = v;
     g.ready_base = 0;
     PG_CUDA(cudaEventCreateWithFlags(&g.ready_ev, cudaEventDisableTiming));
+    {
+        int engines = 0;
+        PG_CUDA(cudaDeviceGetAttribute(&engines, cudaDevAttrAsyncEngineCount, device));
+        const char *env = std::getenv("PG12_HOST_STREAM");
+        g.host_stream = PG12_HOST_STREAM && engines > 0 && !(env && std::strcmp(env, "0") == 0);
+    }
     g.device = device;
     g.init = true;
     return PG_OK;
@@ -1930,9 +1945,6 @@ pg_status pg_merkle_build(const uint64_t *rows, size_t n_leaves, size_t width, u
 
 // Host-row builds: the first copied chunk holds n / FIRST_DIV rows, each next
 // one twice as many, up to n / MAX_DIV; the 16th takes the rest.
-#ifndef PG12_HOST_STREAM
-#define PG12_HOST_STREAM 1  // 0: one leaf launch per copied chunk (the tensor engine's earlier form)
-#endif
 #ifndef PG12_HOST_CHUNK_FIRST_DIV
 #define PG12_HOST_CHUNK_FIRST_DIV 64
 #endif
@@ -1971,7 +1983,7 @@ pg_status pg_merkle_build_host(const uint64_t *rows_host, size_t n_leaves, size_
     PG_CUDA(cudaStreamWaitEvent(g.copy_st, g.host_ev[16], 0));
     const uint64_t chunk_max = n / PG12_HOST_CHUNK_MAX_DIV;
     uint64_t chunk = n / PG12_HOST_CHUNK_FIRST_DIV, first = 0;
-    if (g.engine == 1 && PG12_HOST_STREAM) {
+    if (g.engine == 1 && g.host_stream) {
         // Tensor engine: one leaf launch for all chunks.  After each chunk's
         // rows the copy stream copies the arrival value base + c + 1 into
         // d_ready (a copy-engine write; the waiting kernel needs no other
@@ -1991,24 +2003,20 @@ pg_status pg_merkle_build_host(const uint64_t *rows_host, size_t n_leaves, size_
         cm.base = g.ready_base;
         for (uint32_t c = 0; first < n; ++c) {
             const uint64_t rows_c = (chunk < n - first && c < 15) ? chunk : n - first;
+            PG_CUDA(cudaMemcpyAsync(rows_dev + first * width, rows_host + first * width, rows_c * bytes_per_row,
+                                    cudaMemcpyHostToDevice, g.copy_st));
+            PG_CUDA(cudaMemcpyAsync(g.d_ready, g.ready_vals + cm.base + c + 1, sizeof(uint32_t),
+                                    cudaMemcpyHostToDevice, g.copy_st));
             first += rows_c;
             cm.end[c] = first;
             cm.count = c + 1;
             if (chunk < chunk_max) chunk <<= 1;
         }
         g.ready_base += 16;
-        // the launch first, so that it is on the device while the copies are
-        // still being queued; the reset copy (if any) and this build's values
-        // are ordered on the copy stream
+        // every copy is queued before the launch, so that they run even where
+        // launches block the host until they finish (CUDA_LAUNCH_BLOCKING)
         s = launch_leaves_stream(rows_dev, n, width, nodes, g.d_ready, cm, st);
         if (s != PG_OK) return s;
-        for (uint32_t c = 0; c < cm.count; ++c) {
-            const uint64_t lo = c ? cm.end[c - 1] : 0;
-            PG_CUDA(cudaMemcpyAsync(rows_dev + lo * width, rows_host + lo * width, (cm.end[c] - lo) * bytes_per_row,
-                                    cudaMemcpyHostToDevice, g.copy_st));
-            PG_CUDA(cudaMemcpyAsync(g.d_ready, g.ready_vals + cm.base + c + 1, sizeof(uint32_t),
-                                    cudaMemcpyHostToDevice, g.copy_st));
-        }
         PG_CUDA(cudaEventRecord(g.ready_ev, st));
         s = launch_levels(nodes, n, 1, st);
         if (s != PG_OK) return s;

@@ -87,3 +87,41 @@ def test_host_build_arrival_counter_restarts():
             torch.cuda.synchronize()
             assert torch.equal(nodes, want[i % 2]), i
     assert pg.device_faults() == 0 and faults == 0
+
+
+_CHILD = r"""
+import sys
+sys.path.insert(0, {root!r})
+import torch, paper_2506_09505_gb300 as pg, pg_synth
+pg.load()
+pg.init(0)
+n, w = 1 << 21, 8
+rows = pg_synth.matrix_torch(0x8D00, n, w).pin_memory()
+torch.cuda.synchronize()
+pg.profile_enable(True)
+nodes = pg.merkle_build_host(rows)
+torch.cuda.synchronize()
+kern = pg.profile_read()
+launches = sum(kern[k]["launches"] for k in ("k_tc_sponge:leaves", "k_tc_sponge:rows") if k in kern)
+pg.profile_enable(False)
+ok = torch.equal(nodes, pg.merkle_build(rows.cuda()))
+print("child", launches, ok, pg.device_faults())
+"""
+
+
+@pytest.mark.parametrize("env,streamed", [({"CUDA_LAUNCH_BLOCKING": "1"}, True), ({"PG12_HOST_STREAM": "0"}, False)])
+def test_host_build_in_a_fresh_process(env, streamed):
+    # blocking launches: the chunk copies are queued before the streamed leaf
+    # launch, so it still finds them arriving; PG12_HOST_STREAM=0: one leaf
+    # launch per chunk (the form to use under tools that hold copies back)
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, "-c", _CHILD.format(root=root)], capture_output=True, text=True,
+                         timeout=600, cwd=root, env={**os.environ, **env})
+    assert out.returncode == 0, out.stdout[-2000:] + out.stderr[-2000:]
+    line = [ln for ln in out.stdout.splitlines() if ln.startswith("child ")][-1].split()
+    launches, ok, faults = int(line[1]), line[2] == "True", int(line[3])
+    assert ok and faults == 0
+    assert (launches == 1) == streamed
