@@ -82,20 +82,23 @@ __device__ __forceinline__ uint64_t mul_c(uint64_t a, uint64_t b) { return canon
 // carry out of bit 63 is worth 2^64 = 2^32 - 1 (mod p); adding it back can
 // carry once more only when both inputs were near 2^64, and then the sum is
 // below 2^33.  The carry itself becomes the 32-bit mask 0 - carry (0 or
-// 2^32 - 1), so no compare or select is needed.
+// 2^32 - 1), so no compare or select is needed.  (The flag after an add is
+// a carry; subtract-with-borrow reads it as "no borrow", so the mask takes
+// an add-with-carry and a negation.)
 __device__ __forceinline__ uint64_t add_w(uint64_t a, uint64_t b) {
-    uint32_t s0, s1, m;
-    asm("add.cc.u32 %0, %3, %5;\n\t"
-        "addc.cc.u32 %1, %4, %6;\n\t"
-        "addc.u32 %2, 0, 0;\n\t"
-        "sub.u32 %2, 0, %2;\n\t"
-        "add.cc.u32 %0, %0, %2;\n\t"
+    uint32_t s0, s1;
+    asm("{\n\t.reg .u32 m;\n\t"
+        "add.cc.u32 %0, %2, %4;\n\t"
+        "addc.cc.u32 %1, %3, %5;\n\t"
+        "addc.u32 m, 0, 0;\n\t"
+        "sub.u32 m, 0, m;\n\t"
+        "add.cc.u32 %0, %0, m;\n\t"
         "addc.cc.u32 %1, %1, 0;\n\t"
-        "addc.u32 %2, 0, 0;\n\t"
-        "sub.u32 %2, 0, %2;\n\t"
-        "add.cc.u32 %0, %0, %2;\n\t"
-        "addc.u32 %1, %1, 0;"
-        : "=r"(s0), "=r"(s1), "=r"(m)
+        "addc.u32 m, 0, 0;\n\t"
+        "sub.u32 m, 0, m;\n\t"
+        "add.cc.u32 %0, %0, m;\n\t"
+        "addc.u32 %1, %1, 0;\n\t}"
+        : "=r"(s0), "=r"(s1)
         : "r"(dev::lo32(a)), "r"(dev::hi32(a)), "r"(dev::lo32(b)), "r"(dev::hi32(b)));
     return ((uint64_t)s1 << 32) | s0;
 }
@@ -103,16 +106,17 @@ __device__ __forceinline__ uint64_t add_w(uint64_t a, uint64_t b) {
 // difference was within 2^32 - 1 of -2^64, and then twice is enough.  The
 // borrow-out of subc (0 - 0 - borrow) is already the mask.
 __device__ __forceinline__ uint64_t sub_w(uint64_t a, uint64_t b) {
-    uint32_t d0, d1, m;
-    asm("sub.cc.u32 %0, %3, %5;\n\t"
-        "subc.cc.u32 %1, %4, %6;\n\t"
-        "subc.u32 %2, 0, 0;\n\t"
-        "sub.cc.u32 %0, %0, %2;\n\t"
+    uint32_t d0, d1;
+    asm("{\n\t.reg .u32 m;\n\t"
+        "sub.cc.u32 %0, %2, %4;\n\t"
+        "subc.cc.u32 %1, %3, %5;\n\t"
+        "subc.u32 m, 0, 0;\n\t"
+        "sub.cc.u32 %0, %0, m;\n\t"
         "subc.cc.u32 %1, %1, 0;\n\t"
-        "subc.u32 %2, 0, 0;\n\t"
-        "sub.cc.u32 %0, %0, %2;\n\t"
-        "subc.u32 %1, %1, 0;"
-        : "=r"(d0), "=r"(d1), "=r"(m)
+        "subc.u32 m, 0, 0;\n\t"
+        "sub.cc.u32 %0, %0, m;\n\t"
+        "subc.u32 %1, %1, 0;\n\t}"
+        : "=r"(d0), "=r"(d1)
         : "r"(dev::lo32(a)), "r"(dev::hi32(a)), "r"(dev::lo32(b)), "r"(dev::hi32(b)));
     return ((uint64_t)d1 << 32) | d0;
 }
