@@ -907,6 +907,11 @@ def run_lde(args):
     kern.pop("_dropped", None)
     ms = e0.elapsed_time(e1) / args.steps
     lde_ms = kern["k_ntt_pass"]["total_ms"] / args.steps
+    # the last step's extension and commitment against the oracle's stored outputs
+    g = goldens().get("lde_2e21x8_b1")
+    bit_exact = None
+    if g and (g["log_n"], g["cols"], g["log_blowup"]) == (log_n, cols, log_b):
+        bit_exact = sha256_words(out) == g["out_sha256"] and sha256_words(nodes) == g["nodes_sha256"]
     # one product per butterfly (8 results) and four per input coefficient for the coset factor
     butterflies = (n // 2) * log_n * cols + (big // 2) * log_n * cols
     mul_results = 8 * (butterflies + 4 * n * cols)
@@ -916,7 +921,7 @@ def run_lde(args):
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     print(json.dumps({
         "workload": f"LDE of 2^{log_n} x {cols} evaluations, blowup 2^{log_b}, then the 2^{log_n + log_b} x {cols} Merkle tree",
-        "ms_per_step": ms, "steps": args.steps,
+        "ms_per_step": ms, "steps": args.steps, "bit_exact": bit_exact,
         "lde": {"ms": lde_ms, "launches_per_step": kern["k_ntt_pass"]["launches"] // args.steps,
                 "roofline_alu": {"achieved": mul_results / (lde_ms / 1e3) / 1e12, "peak": _peak_results_per_s() / 1e12,
                                  "unit": "T mul32-results/s",

@@ -10,7 +10,9 @@
                       workload 2, the 2^22 x 8 and 2^22 x 64 trees of
                       workload 3, every tree of the 64-tree batch of
                       workload 4 and the 2^22-leaf served shapes of
-                      workload 5 at widths 8 and 32.  Inputs come from
+                      workload 5 at widths 8 and 32, and the low-degree
+                      extension of the 2^21 x 8 trace (blowup 2) with the
+                      root of its 2^22 x 8 commitment.  Inputs come from
                       pg_synth's workload recipes.
 
 Run from the repository root:
@@ -76,6 +78,15 @@ def full_entries():
     for w in (8, 32):
         out.append((f"serve_2e22_w{w}",
                     lambda w=w: tree_entry(pg_synth.served_rows_seed(22, w), 22, w, threads)))
+
+    def lde():
+        seed, log_n, cols, log_b = pg_synth.config_seed(6), 21, 8, 1
+        ext = oracle.lde_columns(pg_synth.matrix(seed, 1 << log_n, cols), log_b)
+        nodes = oracle.merkle_build(ext, nthreads=threads)
+        return {"seed": hex(seed), "log_n": log_n, "cols": cols, "log_blowup": log_b,
+                "out_sha256": sha256_words(ext), "root": [f"{int(v):016x}" for v in nodes[-1]],
+                "nodes_sha256": sha256_words(nodes)}
+    out.append(("lde_2e21x8_b1", lde))
     return out
 
 

@@ -13,6 +13,8 @@ word must match:
               the autotuned schedule
   workload 5  2^22-leaf served requests of widths 8 and 32, admitted into
               the serving runtime together with smaller requests
+  LDE         the 2^21 x 8 trace extended with blowup 2 (every output word)
+              and its 2^22 x 8 commitment
 
 The path is exact integer arithmetic, so the tolerance is zero.
 """
@@ -128,3 +130,17 @@ def test_served_2e22_requests_in_a_mix():
             srv.release(rid)
     finally:
         srv.close()
+
+
+def test_lde_2e21x8_and_its_commitment():
+    e = GOLD["lde_2e21x8_b1"]
+    evals = pg_synth.matrix_torch(int(e["seed"], 16), 1 << e["log_n"], e["cols"], device="cuda")
+    before = golden_values.sha256_words(evals)
+    out = pg.lde(evals, e["log_blowup"])
+    assert golden_values.sha256_words(out) == e["out_sha256"]
+    assert golden_values.sha256_words(evals) == before
+    nodes, root = pg.merkle_build(out, want_root=True)
+    _check_tree(nodes, root, e)
+    # in place: the input buffer doubles as the scratch buffer
+    work = evals.clone()
+    assert torch.equal(pg.lde(work, e["log_blowup"], scratch=work), out)
