@@ -73,7 +73,8 @@ def test_ntt_round_trip_large():
 
 
 @pytest.mark.parametrize("log_n,log_b,ncols", [(0, 0, 1), (0, 3, 2), (1, 1, 1), (2, 4, 3), (4, 2, 3), (10, 1, 8),
-                                               (10, 0, 5), (11, 3, 5), (13, 2, 9), (12, 1, 16)])
+                                               (10, 0, 5), (11, 3, 5), (13, 2, 9), (12, 1, 16), (4, 6, 2), (9, 5, 8),
+                                               (15, 1, 8), (18, 1, 3)])
 def test_lde_matches_oracle(log_n, log_b, ncols):
     n = 1 << log_n
     evals = pg_synth.matrix(0x7730 + 37 * log_n + 5 * log_b + ncols, n, ncols)
