@@ -432,13 +432,22 @@ def run_ours(args):
         pg.merkle_build_host(host_rows, dev_rows, nodes, want_root=True)
     e_s = time.perf_counter() - t0
     e_clocks = e_sampler.stop()
+    # the same rows as one plain pinned copy: the host link's bandwidth on this machine, which
+    # bounds the end-to-end step when the copy outlasts the leaf hashing it overlaps
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(3):
+        dev_rows.copy_(host_rows, non_blocking=True)
+    torch.cuda.synchronize()
+    h2d_gbs = 3 * rows_np.nbytes / (time.perf_counter() - t0) / 1e9
     if dist is not None:
         t = torch.tensor([e_s], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e_s = float(t.item())
     e2e = {"value": perms * world * e_steps / e_s, "unit": "perms/s",
            "h2d_bytes_per_step": int(rows_np.nbytes), "d2h_bytes_per_step": 32,
-           "ms_per_step": 1e3 * e_s / e_steps, "clocks": e_clocks}
+           "ms_per_step": 1e3 * e_s / e_steps, "clocks": e_clocks,
+           "h2d_copy_gbs": h2d_gbs, "h2d_copy_ms": rows_np.nbytes / h2d_gbs / 1e6}
 
     peaks = measured_peaks()
     sms = props.multi_processor_count
