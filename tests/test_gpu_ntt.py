@@ -63,6 +63,19 @@ def test_ntt_non_canonical_words():
     assert (host(t) == oracle.ntt_columns(x)).all()
 
 
+def test_ntt_2e20x8_against_the_oracle():
+    # two passes of ten bits (radix-8, -8, -4, -4 steps each), forward and inverse, every word
+    n, c = 1 << 20, 8
+    x = pg_synth.matrix(0x7711, n, c)
+    want = oracle.ntt_columns(x)
+    t = dev(x)
+    pg.ntt(t)
+    assert (host(t) == want).all()
+    back = dev(want)
+    pg.ntt(back, inverse=True)
+    assert (host(back) == x).all()
+
+
 def test_ntt_round_trip_large():
     n, c = 1 << 20, 8
     x = pg_synth.matrix_torch(0x7720, n, c, device="cuda")
@@ -74,7 +87,7 @@ def test_ntt_round_trip_large():
 
 @pytest.mark.parametrize("log_n,log_b,ncols", [(0, 0, 1), (0, 3, 2), (1, 1, 1), (2, 4, 3), (4, 2, 3), (10, 1, 8),
                                                (10, 0, 5), (11, 3, 5), (13, 2, 9), (12, 1, 16), (4, 6, 2), (9, 5, 8),
-                                               (15, 1, 8), (18, 1, 3)])
+                                               (15, 1, 8), (18, 1, 3), (18, 2, 4)])
 def test_lde_matches_oracle(log_n, log_b, ncols):
     n = 1 << log_n
     evals = pg_synth.matrix(0x7730 + 37 * log_n + 5 * log_b + ncols, n, ncols)
