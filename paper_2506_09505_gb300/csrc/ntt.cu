@@ -72,6 +72,9 @@ constexpr int kMaxT = 11;        // stages per pass
 #ifndef PG12_NTT_MAXU
 #define PG12_NTT_MAXU 5
 #endif
+#ifndef PG12_NTT_CPASYNC
+#define PG12_NTT_CPASYNC 1       // 1: tile loads as asynchronous copies overlapping the table setup
+#endif
 #ifndef PG12_NTT_TILE_BITS8
 #define PG12_NTT_TILE_BITS8 10   // log2 tile rows with eight columns (64 KiB of words)
 #endif
@@ -445,12 +448,6 @@ __global__ void __launch_bounds__(kThreads) k_ntt_pass(const Pass ps) {
         plan_b |= (DIT ? done : t - done - r) << (4 * nsteps);
         done += r;
     }
-    // beta[l][i] = w_{lo+b+r}^(low0 + l) for step i over bits [b, b + r)
-    for (uint32_t q = threadIdx.x; q < (nsteps << u); q += kThreads) {
-        const uint32_t i = q >> u, l = q & ((1u << u) - 1);
-        const uint32_t top = ((plan_b >> (4 * i)) & 15) + ((plan_r >> (2 * i)) & 3);
-        beta[l][i] = pow_tab(g_ntt.pw[dir], (low0 + l) << (30 - ps.lo - top));
-    }
     // Each thread keeps one (low value, column) slot: kThreads is a multiple
     // of 2^(u + LOG_C) <= 256, so its rows advance by a fixed stride.
     const uint32_t slot = threadIdx.x & ((C << u) - 1);
@@ -459,13 +456,34 @@ __global__ void __launch_bounds__(kThreads) k_ntt_pass(const Pass ps) {
     const bool col_ok = c_me < c_eff;
     {
         // source row of tile row v: ((base | v << lo | l) >> src_shift); src_shift is
-        // 0 or equal to lo, so it is linear in v either way
+        // 0 or equal to lo, so it is linear in v either way.  With PG12_NTT_CPASYNC the
+        // words go to shared memory as asynchronous copies, which stay in flight while
+        // the root-power tables are built.
         const uint64_t r0 = (base | ((uint64_t)v_first << ps.lo) | l_me) >> ps.src_shift;
         const uint64_t rstep = ((uint64_t)v_step << ps.lo) >> ps.src_shift;
         const uint64_t *g = ps.src + r0 * ps.ncols + col0 + c_me;
         const uint64_t gstep = rstep * ps.ncols;
-        for (uint32_t v = v_first, e = threadIdx.x; v < rows; v += v_step, e += kThreads, g += gstep)
+        for (uint32_t v = v_first, e = threadIdx.x; v < rows; v += v_step, e += kThreads, g += gstep) {
+#if PG12_NTT_CPASYNC
+            if (col_ok)
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(tile + e)),
+                             "l"(g)
+                             : "memory");
+            else
+                tile[e] = 0;
+#else
             tile[e] = col_ok ? *g : 0;
+#endif
+        }
+#if PG12_NTT_CPASYNC
+        asm volatile("cp.async.commit_group;" ::: "memory");
+#endif
+    }
+    // beta[l][i] = w_{lo+b+r}^(low0 + l) for step i over bits [b, b + r)
+    for (uint32_t q = threadIdx.x; q < (nsteps << u); q += kThreads) {
+        const uint32_t i = q >> u, l = q & ((1u << u) - 1);
+        const uint32_t top = ((plan_b >> (4 * i)) & 15) + ((plan_r >> (2 * i)) & 3);
+        beta[l][i] = pow_tab(g_ntt.pw[dir], (low0 + l) << (30 - ps.lo - top));
     }
     if (ps.scale == 2) {
         // row factors scale_c 7^bitrev(row) (here lo = u = 0: row = base + v)
@@ -492,6 +510,9 @@ __global__ void __launch_bounds__(kThreads) k_ntt_pass(const Pass ps) {
             }
         }
     }
+#if PG12_NTT_CPASYNC
+    asm volatile("cp.async.wait_all;" ::: "memory");
+#endif
     __syncthreads();
 
     const uint32_t sh = u + LOG_C;
