@@ -337,8 +337,10 @@ pg_status pg_merkle_build(const uint64_t *rows, size_t n_leaves, size_t width, u
 /*
  * pg_merkle_build_host -- pg_merkle_build with the rows in host memory: the
  * same nodes, with the host-to-device copy of the rows overlapped with leaf
- * hashing.  The rows are copied in at most 11 growing chunks on a library
- * stream.  Tensor engine: one leaf launch on `stream` hashes them as they
+ * hashing.  The rows are copied in at most 16 chunks on a library stream
+ * (small first, then n/8 rows, halving again toward the end, so that on a
+ * host link slower than the hashing little work is left once the last copy
+ * lands).  Tensor engine: one leaf launch on `stream` hashes them as they
  * arrive (after each chunk the copy stream writes an arrival counter that
  * the launch waits on, each wait bounded by about 2 s, then the fault shows
  * in pg_device_faults); integer engine: one leaf launch per chunk once its

@@ -1943,8 +1943,13 @@ pg_status pg_merkle_build(const uint64_t *rows, size_t n_leaves, size_t width, u
     return PG_OK;
 }
 
-// Host-row builds: the first copied chunk holds n / FIRST_DIV rows, each next
-// one twice as many, up to n / MAX_DIV; the 16th takes the rest.
+// Host-row builds: the copied chunks' ends (at most 16).  The first chunk
+// holds n / FIRST_DIV rows, each next one twice as many, up to n / MAX_DIV;
+// once at most two of those are left, each chunk takes half of the rest (not
+// below n / FIRST_DIV).  When the host link is faster than the hashing, the
+// copies run ahead and the sizes hardly matter; when it is slower, the
+// hashing keeps pace with the copies and what is left after the last copy
+// lands is one small chunk.
 #ifndef PG12_HOST_CHUNK_FIRST_DIV
 #define PG12_HOST_CHUNK_FIRST_DIV 64
 #endif
@@ -1952,6 +1957,23 @@ pg_status pg_merkle_build(const uint64_t *rows, size_t n_leaves, size_t width, u
 #define PG12_HOST_CHUNK_MAX_DIV 8
 #endif
 static_assert(PG12_HOST_CHUNK_FIRST_DIV >= PG12_HOST_CHUNK_MAX_DIV, "host chunks: the first is the smallest");
+
+uint32_t host_chunks(uint64_t n, uint64_t (&end)[16]) {
+    const uint64_t lo = n / PG12_HOST_CHUNK_FIRST_DIV > 0 ? n / PG12_HOST_CHUNK_FIRST_DIV : 1;
+    const uint64_t hi = n / PG12_HOST_CHUNK_MAX_DIV > lo ? n / PG12_HOST_CHUNK_MAX_DIV : lo;
+    uint64_t grow = lo, first = 0;
+    uint32_t c = 0;
+    while (first < n) {
+        const uint64_t rem = n - first;
+        uint64_t rows = rem <= 2 * hi ? rem / 2 : grow;
+        if (rows < lo) rows = lo;
+        if (rows >= rem || rem - rows < lo || c == 15) rows = rem;
+        first += rows;
+        end[c++] = first;
+        if (grow < hi) grow <<= 1;
+    }
+    return c;
+}
 
 pg_status pg_merkle_build_host(const uint64_t *rows_host, size_t n_leaves, size_t width, uint64_t *rows_dev,
                                uint64_t *nodes, uint64_t *root_out, void *stream) {
@@ -1973,16 +1995,13 @@ pg_status pg_merkle_build_host(const uint64_t *rows_host, size_t n_leaves, size_
         PG_CUDA(cudaMemcpyAsync(rows_dev, rows_host, n * bytes_per_row, cudaMemcpyHostToDevice, st));
         return pg_merkle_build(rows_dev, n_leaves, width, nodes, root_out, stream);
     }
-    // Chunks grow geometrically: the first (n / 64 rows) is small so hashing
-    // starts early, each next one doubles up to n / 8.  A copy runs several
-    // times faster than hashing consumes rows, so every later chunk arrives
-    // before the one ahead of it is hashed; at most 11 chunks.
-    // The copies into rows_dev wait for work already queued on `st` (an
-    // earlier build may still read it).
+    // The chunks (host_chunks): small first so hashing starts early, then
+    // n / 8 rows, halving again toward the end.  The copies into rows_dev wait
+    // for work already queued on `st` (an earlier build may still read it).
     PG_CUDA(cudaEventRecord(g.host_ev[16], st));
     PG_CUDA(cudaStreamWaitEvent(g.copy_st, g.host_ev[16], 0));
-    const uint64_t chunk_max = n / PG12_HOST_CHUNK_MAX_DIV;
-    uint64_t chunk = n / PG12_HOST_CHUNK_FIRST_DIV, first = 0;
+    uint64_t ends[16];
+    const uint32_t nchunks = host_chunks(n, ends);
     if (g.engine == 1 && g.host_stream) {
         // Tensor engine: one leaf launch for all chunks.  After each chunk's
         // rows the copy stream copies the arrival value base + c + 1 into
@@ -2001,16 +2020,14 @@ pg_status pg_merkle_build_host(const uint64_t *rows_host, size_t n_leaves, size_
         }
         dev::ChunkMap cm = {};
         cm.base = g.ready_base;
-        for (uint32_t c = 0; first < n; ++c) {
-            const uint64_t rows_c = (chunk < n - first && c < 15) ? chunk : n - first;
+        for (uint32_t c = 0; c < nchunks; ++c) {
+            const uint64_t first = c ? ends[c - 1] : 0, rows_c = ends[c] - first;
             PG_CUDA(cudaMemcpyAsync(rows_dev + first * width, rows_host + first * width, rows_c * bytes_per_row,
                                     cudaMemcpyHostToDevice, g.copy_st));
             PG_CUDA(cudaMemcpyAsync(g.d_ready, g.ready_vals + cm.base + c + 1, sizeof(uint32_t),
                                     cudaMemcpyHostToDevice, g.copy_st));
-            first += rows_c;
-            cm.end[c] = first;
+            cm.end[c] = ends[c];
             cm.count = c + 1;
-            if (chunk < chunk_max) chunk <<= 1;
         }
         g.ready_base += 16;
         // every copy is queued before the launch, so that they run even where
@@ -2026,17 +2043,14 @@ pg_status pg_merkle_build_host(const uint64_t *rows_host, size_t n_leaves, size_
         }
         return PG_OK;
     }
-    for (uint32_t c = 0; first < n; ++c) {
-        // the 16th chunk takes whatever is left (16 copy events)
-        const uint64_t rows_c = (chunk < n - first && c < 15) ? chunk : n - first;
+    for (uint32_t c = 0; c < nchunks; ++c) {
+        const uint64_t first = c ? ends[c - 1] : 0, rows_c = ends[c] - first;
         PG_CUDA(cudaMemcpyAsync(rows_dev + first * width, rows_host + first * width, rows_c * bytes_per_row,
                                 cudaMemcpyHostToDevice, g.copy_st));
         PG_CUDA(cudaEventRecord(g.host_ev[c], g.copy_st));
         PG_CUDA(cudaStreamWaitEvent(st, g.host_ev[c], 0));
         s = launch_leaves(rows_dev + first * width, rows_c, width, nodes + 4 * first, st);
         if (s != PG_OK) return s;
-        first += rows_c;
-        if (chunk < chunk_max) chunk <<= 1;
     }
     s = launch_levels(nodes, n, 1, st);
     if (s != PG_OK) return s;
